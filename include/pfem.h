@@ -1,0 +1,184 @@
+/*
+ * pfem.h -- C ABI of the GB300 particle <-> fixed-mesh projection library (libpfem.so).
+ *
+ * The library implements, as CUDA kernels for sm_103a, the projection round trip of
+ * Duque & Espanol, "Rapid convergence for simulations that project from particles onto a
+ * fixed mesh" (arXiv 1610.05266), in 2D on the unit periodic square:
+ *
+ *   P2M  (Sec. 2.2, eq. p2m):  alpha_i  = sum_mu alpha_mu psi^p_mu(r_i)   at mesh nodes
+ *   M2P  (Sec. 2.2, eq. m2p):  alpha_mu = sum_i  alpha_i  psi^m_i(r_mu)   at particles
+ *
+ * psi^p is either the linear finite-element shape function on the particles' Delaunay
+ * triangulation (App. B, eqs. C0-C1) or the quadratically consistent shape function of
+ * App. B eq. (phiquad), psi_mu = phi_mu + sum_{nu sigma} A_{mu nu sigma} phi_nu phi_sigma,
+ * with A for each Delaunay edge the minimum-norm solution of eqs. (A0), (A1), (condquad)
+ * over the edge's stencil (both endpoints and their Delaunay neighbours; App. A solves it
+ * "by SVD with rank detection").  psi^m is linear FE on the fixed structured mesh.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Domain: unit periodic square.  Positions are (x, y) pairs, any real values with
+ *    |x|,|y| < 2^20; they are taken modulo 1.
+ *  - Mesh: n x n nodes including the stored periodic image row and column (n >= 9),
+ *    spacing H = 1/(n-1).  Node (I, J) is at (I*H, J*H) and its C values are stored at
+ *    mesh_vals[(J*n + I)*C + c].  Row/column n-1 hold copies of row/column 0.  Each cell is
+ *    split along its (i,j)->(i+1,j+1) diagonal.
+ *  - Topology (bins, Delaunay, point location) uses fixed-point coordinates
+ *    q = round_half_even(x * 2^32) mod 2^32; Delaunay ties among cocircular particles are
+ *    broken by perturbing lifted heights in the order of the key (qy << 32 | qx).
+ *    Duplicate particles are rejected (PFEM_ERR_DEGENERATE).
+ *  - Particle bins: an nb x nb grid, bin (bx, by) = ((qx*nb) >> 32, (qy*nb) >> 32), bin id
+ *    by*nb + bx.  pfem_default_bins() picks nb for about 4 particles per bin.
+ *  - Arrays are row-major and contiguous.  All device pointers are CUDA device (or managed)
+ *    memory allocated by the caller; the library allocates nothing.  `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).  Every call is
+ *    asynchronous on `stream`; host-detectable argument errors come back as the return
+ *    code and launch nothing.
+ *  - Errors found on the device (capacity, degeneracy, iteration caps) are recorded in the
+ *    status word at the start of the workspace `ws`; pfem_read_status() synchronises the
+ *    stream and returns it.  Kernels never trap and every loop is bounded.
+ *  - Storage dtypes: positions PFEM_F64 or PFEM_F32; particle and mesh values PFEM_F64,
+ *    PFEM_F32 or PFEM_BF16 (BF16 is storage only; arithmetic is FP32).  Arithmetic is FP64
+ *    when values are PFEM_F64, FP32 otherwise; `solve` selects the precision of the 6x6
+ *    moment systems independently.
+ */
+#ifndef PFEM_H
+#define PFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PFEM_OK = 0,
+    PFEM_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported dtype combination */
+    PFEM_ERR_CUDA = 2,          /* a CUDA launch or runtime call failed */
+    PFEM_ERR_WORKSPACE = 3,     /* ws_bytes smaller than the matching *_workspace_size() */
+    PFEM_ERR_CAPACITY = 4,      /* device: star > PFEM_KMAX, stencil or weight list overflow,
+                                   search region exhausted */
+    PFEM_ERR_DEGENERATE = 5,    /* device: duplicate particles or rank-deficient moments */
+    PFEM_ERR_TIMEOUT = 6        /* device: a bounded loop hit its iteration cap */
+} pfem_status;
+
+typedef enum { PFEM_F64 = 0, PFEM_F32 = 1, PFEM_BF16 = 2 } pfem_dtype;
+typedef enum { PFEM_SHAPE_LINEAR = 0, PFEM_SHAPE_QUADRATIC = 1 } pfem_shape;
+typedef enum {
+    PFEM_SOLVE_F64 = 0,         /* moment assembly and Cholesky in FP64 */
+    PFEM_SOLVE_F32 = 1,         /* in FP32 after centring/scaling by the edge length */
+    PFEM_SOLVE_F32_REFINED = 2  /* FP32 Cholesky + one refinement step, FP64 residual */
+} pfem_solve;
+typedef enum { PFEM_BACKWARD_RECOMPUTE = 0, PFEM_BACKWARD_CHECKPOINT = 1 } pfem_backward_mode;
+
+#define PFEM_KMAX 16        /* max Delaunay neighbours of one particle */
+#define PFEM_KW_MAX 64      /* max weights per node in the explicit-weight form */
+
+/* Version of this ABI. */
+int pfem_abi_version(void);
+
+/* Human-readable name of a status code. */
+const char *pfem_status_string(pfem_status s);
+
+/* Bins per side for N particles on a mesh of n nodes per side: about 4 particles per bin,
+ * at least 8 bins per side. */
+int32_t pfem_default_bins(int32_t n, int64_t N);
+
+/* Bytes of workspace `ws` needed by the calls below for these sizes (>= 256). */
+size_t pfem_workspace_size(int32_t n, int32_t nb, int64_t N, int32_t C);
+
+/* Status word recorded by device code in `ws` since the last reset; synchronises `stream`
+ * (the only synchronising call of the library).  *status_host = pfem_status value,
+ * *detail_host = index of the first failing node or particle (or -1). */
+pfem_status pfem_read_status(const void *ws, int32_t *status_host, int64_t *detail_host,
+                             void *stream);
+
+/* Reset the device status word in `ws` to PFEM_OK (asynchronous). */
+pfem_status pfem_reset_status(void *ws, void *stream);
+
+/* a1-a2: canonicalise positions to fixed point and bin the particles with a stable
+ * counting sort, slots ordered by (bin, original index).
+ *   pos        [N,2] pos_t, original order (device)
+ *   cell_start [nb*nb+1] int32 out: slots of bin b are cell_start[b] .. cell_start[b+1]-1
+ *   perm       [N] int32 out: original index of the particle in each slot
+ *   pos_sorted [N,2] pos_t out: pos[perm[s]]
+ *   q_sorted   [N,2] uint32 out: fixed-point coordinates of pos_sorted
+ *   ws         workspace of pfem_workspace_size(n, nb, N, C) bytes
+ * No paper counterpart: the paper locates particles through CGAL (App. A). */
+pfem_status pfem_build_cells(int32_t nb, int64_t N, const void *pos, pfem_dtype pos_t,
+                             int32_t *cell_start, int32_t *perm, void *pos_sorted,
+                             uint32_t *q_sorted, void *ws, size_t ws_bytes, void *stream);
+
+/* Delaunay stars (App. B: neighbours = particles joined by a Delaunay edge) of every
+ * particle, counter-clockwise, in slot indices: nbrs [N, PFEM_KMAX] int32 (unused entries
+ * -1), counts [N] int32.  Diagnostic entry point; the projections compute the stars they
+ * need on the fly. */
+pfem_status pfem_delaunay_stars(int32_t nb, int64_t N, const uint32_t *q_sorted,
+                                const int32_t *cell_start, int32_t *nbrs, int32_t *counts,
+                                void *ws, size_t ws_bytes, void *stream);
+
+/* Explicit P2M weights per node (eq. p2m with the chosen shape functions):
+ * w_idx [n*n, K] int32 slot indices (-1 = unused) and w [n*n, K] weights (FP64 when
+ * w_t == PFEM_F64, else FP32), so that alpha_i = sum_k w[i,k] alpha[slot w_idx[i,k]].
+ * K <= PFEM_KW_MAX; a node with more distinct particles records PFEM_ERR_CAPACITY.
+ * Used by the checkpointed backward and by pfem_project_p2m with given weights. */
+pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+                                 pfem_dtype pos_t, const uint32_t *q_sorted,
+                                 const int32_t *cell_start, pfem_shape shape, pfem_solve solve,
+                                 int32_t K, int32_t *w_idx, void *w, pfem_dtype w_t, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/* P2M (Sec. 2.2 eq. p2m) at all n*n nodes (image row/column included).
+ *   vals      [N, C] val_t: if perm != NULL, vals are in ORIGINAL particle order and slot s
+ *             reads vals[perm[s]]; if perm == NULL, vals are already in slot order
+ *   w_idx, w  NULL => shape functions computed on the fly (fused); else the weights from
+ *             pfem_shape_quadratic (K per node, dtype w_t) are applied
+ *   mesh_vals [n, n, C] val_t out
+ * C in 1..8. */
+pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+                             pfem_dtype pos_t, const uint32_t *q_sorted,
+                             const int32_t *cell_start, const int32_t *perm, int32_t C,
+                             const void *vals, pfem_dtype val_t, pfem_shape shape,
+                             pfem_solve solve, const int32_t *w_idx, const void *w, int32_t K,
+                             pfem_dtype w_t, void *mesh_vals, void *ws, size_t ws_bytes,
+                             void *stream);
+
+/* M2P (Sec. 2.2 eq. m2p) with linear FE on the structured mesh, per particle in the order
+ * of `pos`:  vals [N, C] val_t out,  mesh_vals [n, n, C] val_t.  C in 1..8.  Needs no
+ * workspace and records no device errors. */
+pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
+                            int32_t C, const void *mesh_vals, void *vals, pfem_dtype val_t,
+                            void *stream);
+
+/* Adjoint of P2M with respect to particle values and positions, for an upstream gradient
+ * grad_mesh [n, n, C] (each stored entry, image copies included, is its own output):
+ *   grad_vals [N, C] out (original order when perm != NULL, slot order otherwise)
+ *   grad_pos  [N, 2] out, same order; NULL skips the position gradient
+ * Topology is held fixed.  mode RECOMPUTE rebuilds the shape functions; mode CHECKPOINT
+ * reads w_idx/w from pfem_shape_quadratic for the value gradient (positions are always
+ * recomputed).  Deterministic: no atomics.  Values must be FP32 or FP64. */
+pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+                                  pfem_dtype pos_t, const uint32_t *q_sorted,
+                                  const int32_t *cell_start, const int32_t *perm, int32_t C,
+                                  const void *vals, pfem_dtype val_t, pfem_shape shape,
+                                  pfem_solve solve, pfem_backward_mode mode,
+                                  const int32_t *w_idx, const void *w, int32_t K,
+                                  pfem_dtype w_t, const void *grad_mesh, void *grad_vals,
+                                  void *grad_pos, void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of M2P for an upstream gradient grad_vals [N, C] (order of pos):
+ *   grad_mesh [n, n, C] out: into the stored entry each forward read used
+ *   grad_pos  [N, 2] out (NULL skips): grad_vals . gradient of the linear FE field
+ * Deterministic: a per-node gather over the bins' particles (bins must be the
+ * pfem_build_cells output for the same positions).  FP32 or FP64 values. */
+pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const void *pos,
+                                     pfem_dtype pos_t, const int32_t *cell_start,
+                                     const int32_t *perm, int32_t C, const void *mesh_vals,
+                                     const void *grad_vals, pfem_dtype val_t, void *grad_mesh,
+                                     void *grad_pos, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFEM_H */

@@ -1,0 +1,195 @@
+"""Python binding of the C ABI (one function per entry point, same names) plus a small
+buffer-owning helper.  Only argument marshalling happens here: every step of the path runs
+in libpfem's CUDA kernels; torch only provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import torch
+
+from . import _lib as L
+from ._lib import (PFEM_BACKWARD_CHECKPOINT, PFEM_BACKWARD_RECOMPUTE, PFEM_F32, PFEM_F64,  # noqa: F401
+                   PFEM_KMAX, PFEM_KW_MAX, PFEM_SHAPE_LINEAR, PFEM_SHAPE_QUADRATIC,
+                   PFEM_SOLVE_F32, PFEM_SOLVE_F32_REFINED, PFEM_SOLVE_F64, PfemError, check,
+                   dtype_code, ptr, stream_ptr)
+
+
+def pfem_abi_version() -> int:
+    return L.load().pfem_abi_version()
+
+
+def pfem_default_bins(n: int, N: int) -> int:
+    return int(L.load().pfem_default_bins(n, N))
+
+
+def pfem_workspace_size(n: int, nb: int, N: int, C: int) -> int:
+    return int(L.load().pfem_workspace_size(n, nb, N, C))
+
+
+def pfem_read_status(ws: torch.Tensor, stream=None) -> Tuple[int, int]:
+    code, detail = ctypes.c_int32(0), ctypes.c_int64(0)
+    check(L.load().pfem_read_status(ptr(ws), ctypes.byref(code), ctypes.byref(detail),
+                                    stream_ptr(stream)), "pfem_read_status")
+    return code.value, detail.value
+
+
+def pfem_reset_status(ws: torch.Tensor, stream=None):
+    check(L.load().pfem_reset_status(ptr(ws), stream_ptr(stream)), "pfem_reset_status")
+
+
+def pfem_build_cells(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, ws, stream=None):
+    check(L.load().pfem_build_cells(nb, N, ptr(pos), dtype_code(pos.dtype), ptr(cell_start),
+                                    ptr(perm), ptr(pos_sorted), ptr(q_sorted), ptr(ws),
+                                    ws.numel() * ws.element_size(), stream_ptr(stream)),
+          "pfem_build_cells")
+
+
+def pfem_delaunay_stars(nb, N, q_sorted, cell_start, nbrs, counts, ws, stream=None):
+    check(L.load().pfem_delaunay_stars(nb, N, ptr(q_sorted), ptr(cell_start), ptr(nbrs),
+                                       ptr(counts), ptr(ws), ws.numel() * ws.element_size(),
+                                       stream_ptr(stream)), "pfem_delaunay_stars")
+
+
+def pfem_shape_quadratic(n, nb, N, pos_sorted, q_sorted, cell_start, shape, solve, K, w_idx, w,
+                         ws, stream=None):
+    check(L.load().pfem_shape_quadratic(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
+                                        ptr(q_sorted), ptr(cell_start), shape, solve, K,
+                                        ptr(w_idx), ptr(w), dtype_code(w.dtype), ptr(ws),
+                                        ws.numel() * ws.element_size(), stream_ptr(stream)),
+          "pfem_shape_quadratic")
+
+
+def pfem_project_p2m(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape, solve,
+                     w_idx, w, K, mesh_vals, ws, stream=None):
+    w_t = dtype_code(w.dtype) if w is not None else PFEM_F32
+    check(L.load().pfem_project_p2m(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
+                                    ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
+                                    dtype_code(vals.dtype), shape, solve, ptr(w_idx), ptr(w), K,
+                                    w_t, ptr(mesh_vals), ptr(ws), ws.numel() * ws.element_size(),
+                                    stream_ptr(stream)), "pfem_project_p2m")
+
+
+def pfem_interp_m2p(n, N, pos, C, mesh_vals, vals, stream=None):
+    check(L.load().pfem_interp_m2p(n, N, ptr(pos), dtype_code(pos.dtype), C, ptr(mesh_vals),
+                                   ptr(vals), dtype_code(vals.dtype), stream_ptr(stream)),
+          "pfem_interp_m2p")
+
+
+def pfem_project_backward(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape,
+                          solve, mode, w_idx, w, K, grad_mesh, grad_vals, grad_pos, ws,
+                          stream=None):
+    w_t = dtype_code(w.dtype) if w is not None else PFEM_F32
+    check(L.load().pfem_project_backward(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
+                                         ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
+                                         dtype_code(vals.dtype), shape, solve, mode, ptr(w_idx),
+                                         ptr(w), K, w_t, ptr(grad_mesh), ptr(grad_vals),
+                                         ptr(grad_pos), ptr(ws), ws.numel() * ws.element_size(),
+                                         stream_ptr(stream)), "pfem_project_backward")
+
+
+def pfem_interp_m2p_backward(n, nb, N, pos, cell_start, perm, C, mesh_vals, grad_vals, grad_mesh,
+                             grad_pos, stream=None):
+    check(L.load().pfem_interp_m2p_backward(n, nb, N, ptr(pos), dtype_code(pos.dtype),
+                                            ptr(cell_start), ptr(perm), C, ptr(mesh_vals),
+                                            ptr(grad_vals), dtype_code(grad_vals.dtype),
+                                            ptr(grad_mesh), ptr(grad_pos), stream_ptr(stream)),
+          "pfem_interp_m2p_backward")
+
+
+@dataclass
+class Cells:
+    """Device buffers of one binned particle set (output of pfem_build_cells)."""
+    n: int
+    nb: int
+    N: int
+    cell_start: torch.Tensor
+    perm: torch.Tensor
+    pos_sorted: torch.Tensor
+    q_sorted: torch.Tensor
+    ws: torch.Tensor
+
+
+class Projector:
+    """Owns the device buffers for one problem size and runs the round trip through the ABI."""
+
+    def __init__(self, n: int, N: int, C: int = 1, nb: Optional[int] = None,
+                 pos_dtype: torch.dtype = torch.float64, device="cuda"):
+        self.n, self.N, self.C = n, N, C
+        self.nb = nb if nb is not None else pfem_default_bins(n, N)
+        self.device = torch.device(device)
+        ws_bytes = pfem_workspace_size(n, self.nb, N, C)
+        dev = self.device
+        self.cells = Cells(
+            n, self.nb, N,
+            torch.empty(self.nb * self.nb + 1, dtype=torch.int32, device=dev),
+            torch.empty(max(N, 1), dtype=torch.int32, device=dev),
+            torch.empty((max(N, 1), 2), dtype=pos_dtype, device=dev),
+            torch.empty((max(N, 1), 2), dtype=torch.int32, device=dev),
+            torch.zeros((ws_bytes + 15) // 16 * 2, dtype=torch.float64, device=dev),
+        )
+
+    @property
+    def ws(self) -> torch.Tensor:
+        return self.cells.ws
+
+    def build(self, pos: torch.Tensor, stream=None):
+        c = self.cells
+        pfem_build_cells(self.nb, self.N, pos, c.cell_start, c.perm, c.pos_sorted, c.q_sorted,
+                         c.ws, stream)
+        return c
+
+    def p2m(self, vals: torch.Tensor, shape=PFEM_SHAPE_QUADRATIC, solve=None, out=None,
+            sorted_vals: bool = False, weights=None, stream=None) -> torch.Tensor:
+        c = self.cells
+        C = vals.shape[1]
+        if solve is None:
+            solve = PFEM_SOLVE_F64 if vals.dtype == torch.float64 else PFEM_SOLVE_F32
+        if out is None:
+            out = torch.empty((self.n, self.n, C), dtype=vals.dtype, device=vals.device)
+        w_idx, w = (weights if weights is not None else (None, None))
+        K = w_idx.shape[1] if w_idx is not None else 0
+        pfem_project_p2m(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
+                         None if sorted_vals else c.perm, C, vals, shape, solve, w_idx, w, K, out,
+                         c.ws, stream)
+        return out
+
+    def shape_weights(self, shape=PFEM_SHAPE_QUADRATIC, solve=None, K: int = 32,
+                      w_dtype=None, stream=None):
+        c = self.cells
+        w_dtype = w_dtype or c.pos_sorted.dtype
+        if solve is None:
+            solve = PFEM_SOLVE_F64 if w_dtype == torch.float64 else PFEM_SOLVE_F32
+        nn = self.n * self.n
+        w_idx = torch.empty((nn, K), dtype=torch.int32, device=self.device)
+        w = torch.empty((nn, K), dtype=w_dtype, device=self.device)
+        pfem_shape_quadratic(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
+                             shape, solve, K, w_idx, w, c.ws, stream)
+        return w_idx, w
+
+    def stars(self, stream=None):
+        c = self.cells
+        nbrs = torch.empty((self.N, PFEM_KMAX), dtype=torch.int32, device=self.device)
+        counts = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        pfem_delaunay_stars(self.nb, self.N, c.q_sorted, c.cell_start, nbrs, counts, c.ws, stream)
+        return nbrs, counts
+
+    def m2p(self, pos: torch.Tensor, mesh: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        C = mesh.shape[-1]
+        if out is None:
+            out = torch.empty((pos.shape[0], C), dtype=mesh.dtype, device=mesh.device)
+        pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream)
+        return out
+
+    def status(self, stream=None) -> Tuple[int, int]:
+        return pfem_read_status(self.cells.ws, stream)
+
+    def reset_status(self, stream=None):
+        pfem_reset_status(self.cells.ws, stream)
+
+    def check(self, what: str = "device status", stream=None):
+        code, detail = self.status(stream)
+        if code != 0:
+            raise PfemError(code, f"{what} (first failure at index {detail})")

@@ -1,0 +1,325 @@
+// geom.cuh -- local Delaunay geometry on the GPU (App. B: Delaunay triangulation of the
+// particles, whose edges define "neighbours"; linear FE shape functions on its triangles).
+//
+// Nothing here builds a global triangulation.  A thread computes the Delaunay star of one
+// particle by gift-wrapping over the particles of the bins around it, and certifies every
+// triangle it returns by checking that the triangle's circumcircle lies inside the searched
+// region (so no particle outside it can be inside the circle); otherwise the region grows.
+//
+// Predicates are exact on 32-bit fixed-point coordinates (differences as signed 32-bit ints
+// give the minimal image on the torus): orientation in 64-bit integers; incircle first in
+// FP32 with a forward error bound, and in 128-bit integers when the filter cannot decide.
+// Ties (four cocircular particles) are broken by perturbing the lifted heights, the particle
+// with the largest key (qy << 32 | qx) taking the dominant perturbation.
+#pragma once
+
+#include "common.cuh"
+
+namespace pfem {
+
+constexpr int KMAX = PFEM_KMAX;
+
+struct Bins {
+    const uint2 *__restrict__ q;      // [N] fixed-point (x, y) in slot order
+    const int *__restrict__ start;    // [nb*nb + 1]
+    int nb;
+    int rmax;                         // largest search radius (bins) tried before giving up
+};
+
+__device__ __forceinline__ int2 rel(uint2 a, uint2 o)
+{
+    return make_int2((int)(a.x - o.x), (int)(a.y - o.y));
+}
+
+__device__ __forceinline__ unsigned long long key_of(uint2 q)
+{
+    return ((unsigned long long)q.y << 32) | q.x;
+}
+
+// a x b for relative coordinates (|components| < 2^30): exact in 64 bits.
+__device__ __forceinline__ long long cross(int2 a, int2 b)
+{
+    return (long long)a.x * b.y - (long long)a.y * b.x;
+}
+
+// Orientation of (a, b, c) given relative to a common origin: (b - a) x (c - a).
+__device__ __forceinline__ long long orient3(int2 a, int2 b, int2 c)
+{
+    int2 u = make_int2(b.x - a.x, b.y - a.y), w = make_int2(c.x - a.x, c.y - a.y);
+    return cross(u, w);
+}
+
+// A region: bins [bx-R, bx+R] x [by-R, by+R] around the bin of a point, and the guaranteed
+// clearance from that point to the region's edge on each side (fixed-point units).
+struct Region {
+    int bx, by, R;
+    float cl_lo_x, cl_hi_x, cl_lo_y, cl_hi_y;
+};
+
+__device__ __forceinline__ Region make_region(const Bins &B, uint2 p, int R)
+{
+    Region g;
+    g.R = R;
+    g.bx = bin_of(p.x, B.nb);
+    g.by = bin_of(p.y, B.nb);
+    const long long bw = (long long)((1ull << 32) / (unsigned long long)B.nb);
+    g.cl_lo_x = (float)((long long)p.x - bin_lo(g.bx, B.nb) + R * bw);
+    g.cl_hi_x = (float)(bin_lo(g.bx + 1, B.nb) - 1 - (long long)p.x + R * bw);
+    g.cl_lo_y = (float)((long long)p.y - bin_lo(g.by, B.nb) + R * bw);
+    g.cl_hi_y = (float)(bin_lo(g.by + 1, B.nb) - 1 - (long long)p.y + R * bw);
+    return g;
+}
+
+// Visit every slot of the region's bins once (rows are contiguous slot ranges unless they
+// wrap around the torus).
+template <typename F>
+__device__ __forceinline__ void for_region(const Bins &B, const Region &g, F &&f)
+{
+    const int nb = B.nb;
+    for (int dy = -g.R; dy <= g.R; ++dy) {
+        int by = g.by + dy;
+        by += by < 0 ? nb : 0;
+        by -= by >= nb ? nb : 0;
+        const int *row = B.start + (long long)by * nb;
+        int x0 = g.bx - g.R, x1 = g.bx + g.R;       // inclusive
+        if (x0 >= 0 && x1 < nb) {
+            int s1 = __ldg(row + x1 + 1);
+            for (int s = __ldg(row + x0); s < s1; ++s) f(s);
+        } else {
+            int a0 = x0 < 0 ? x0 + nb : x0;          // wrapped first run: [a0, nb)
+            int a1 = x1 >= nb ? x1 - nb : x1;        // second run: [0, a1]
+            if (x0 < 0) {
+                int s1 = __ldg(row + nb);
+                for (int s = __ldg(row + a0); s < s1; ++s) f(s);
+                int t1 = __ldg(row + x1 + 1);
+                for (int s = __ldg(row); s < t1; ++s) f(s);
+            } else {
+                int s1 = __ldg(row + nb);
+                for (int s = __ldg(row + x0); s < s1; ++s) f(s);
+                int t1 = __ldg(row + a1 + 1);
+                for (int s = __ldg(row); s < t1; ++s) f(s);
+            }
+        }
+    }
+}
+
+// Circle through the origin v and points a, b (v, a, b counter-clockwise), as the lifted
+// determinant det3(c) = K |c|^2 + P cx + Q cy: c is strictly inside iff det3(c) < 0.
+// P, Q are rounded to FP32; Pa, Qa bound the magnitudes of the terms they were formed from.
+struct Circ {
+    float K, P, Q, Pa, Qa;
+};
+
+__device__ __forceinline__ Circ make_circ(int2 a, int2 b)
+{
+    Circ c;
+    const long long la = (long long)a.x * a.x + (long long)a.y * a.y;
+    const long long lb = (long long)b.x * b.x + (long long)b.y * b.y;
+    const float fla = (float)la, flb = (float)lb;
+    const float t1 = flb * (float)a.y, t2 = fla * (float)b.y;
+    const float t3 = fla * (float)b.x, t4 = flb * (float)a.x;
+    c.K = (float)cross(a, b);
+    c.P = t1 - t2;
+    c.Pa = fabsf(t1) + fabsf(t2);
+    c.Q = t3 - t4;
+    c.Qa = fabsf(t3) + fabsf(t4);
+    return c;
+}
+
+// FP32 filter: +1 strictly inside, -1 strictly outside, 0 undecided.  The bound 2^-20 (16
+// units of FP32 rounding) times the sum of absolute terms covers the rounding of the inputs,
+// of K, P, Q and of the evaluation (at most about 8 roundings on any path).
+__device__ __forceinline__ int circ_filter(const Circ &c, int2 p)
+{
+    const float x = (float)p.x, y = (float)p.y;
+    const float l = fmaf(x, x, y * y);
+    const float det = fmaf(c.K, l, fmaf(c.P, x, c.Q * y));
+    const float mag = fmaf(c.K, l, fmaf(c.Pa, fabsf(x), c.Qa * fabsf(y)));
+    const float bound = 9.5367431640625e-07f * mag;
+    return det < -bound ? 1 : (det > bound ? -1 : 0);
+}
+
+// Exact incircle with the tie-break.  Points are relative to v (the origin); qv, qa, qb, qc
+// are the absolute fixed-point coordinates that give the keys.  Returns +1 when c is inside
+// circle(v, a, b) (perturbed), -1 otherwise.
+__device__ __noinline__ int incircle_exact(int2 a, int2 b, int2 c, uint2 qv, uint2 qa,
+                                           uint2 qb, uint2 qc)
+{
+    const long long la = (long long)a.x * a.x + (long long)a.y * a.y;
+    const long long lb = (long long)b.x * b.x + (long long)b.y * b.y;
+    const long long lc = (long long)c.x * c.x + (long long)c.y * c.y;
+    const __int128 det = (__int128)la * cross(b, c) - (__int128)lb * cross(a, c) +
+                         (__int128)lc * cross(a, b);
+    if (det < 0) return 1;
+    if (det > 0) return -1;
+    // Lifting v, a, b or c by the dominant infinitesimal changes the lifted 4x4 determinant
+    // (positive inside) by the cofactor of that point: orient(a,b,c), -orient(v,b,c),
+    // orient(v,a,c), -orient(v,a,b) respectively.
+    const unsigned long long kv = key_of(qv), ka = key_of(qa), kb = key_of(qb), kc = key_of(qc);
+    unsigned long long km = kv;
+    int m = 0;
+    if (ka > km) { km = ka; m = 1; }
+    if (kb > km) { km = kb; m = 2; }
+    if (kc > km) { km = kc; m = 3; }
+    long long o;
+    switch (m) {
+    case 0: o = orient3(a, b, c); break;
+    case 1: o = -cross(b, c); break;
+    case 2: o = cross(a, c); break;
+    default: o = -cross(a, b); break;
+    }
+    return o > 0 ? 1 : -1;
+}
+
+// Apex of the Delaunay triangle to the left of the directed edge v -> w, among the region's
+// particles.  Returns its slot, or -1 when there is none or its circumcircle is not certified
+// to lie inside the region.
+__device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, const Region &g)
+{
+    const int2 dw = rel(pw, pv);
+    int best = -1;
+    int2 db = make_int2(0, 0);
+    uint2 qb = make_uint2(0, 0);
+    Circ cb;
+    cb.K = cb.P = cb.Q = cb.Pa = cb.Qa = 0.f;
+    for_region(B, g, [&](int s) {
+        const uint2 qs = __ldg(B.q + s);
+        const int2 dc = rel(qs, pv);
+        if (cross(dw, dc) <= 0) return;               // not strictly left of v -> w
+        if (best >= 0) {
+            int t = circ_filter(cb, dc);
+            if (t == 0) t = incircle_exact(dw, db, dc, pv, pw, qb, qs);
+            if (t < 0) return;
+        }
+        best = s;
+        db = dc;
+        qb = qs;
+        cb = make_circ(dw, dc);
+    });
+    if (best < 0) return -1;
+    // Certify: centre (-P/2K, -Q/2K) relative to v, radius |centre|, plus an error margin far
+    // above the FP32 rounding of P, Q, K.
+    const float inv2k = 0.5f / cb.K;
+    const float cx = -cb.P * inv2k, cy = -cb.Q * inv2k;
+    const float r = sqrtf(fmaf(cx, cx, cy * cy));
+    const float err = 1e-5f * (cb.Pa + cb.Qa) * (2.f * inv2k) + 64.f;
+    const float ext = r + err;
+    if (cx - ext < -g.cl_lo_x || cx + ext > g.cl_hi_x || cy - ext < -g.cl_lo_y ||
+        cy + ext > g.cl_hi_y)
+        return -1;
+    return best;
+}
+
+// Counter-clockwise Delaunay star of slot v into nbrs[0..count).  Returns count >= 3, or
+// -PFEM_ERR_* on failure.
+__device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
+{
+    const uint2 pv = __ldg(B.q + v);
+    for (int R = R0; R <= B.rmax; ++R) {
+        const Region g = make_region(B, pv, R);
+        int u0 = -1;
+        long long d2b = 0x7fffffffffffffffLL;
+        bool dup = false;
+        for_region(B, g, [&](int s) {
+            if (s == v) return;
+            const int2 d = rel(__ldg(B.q + s), pv);
+            const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
+            dup |= d2 == 0;
+            if (d2 < d2b || (d2 == d2b && s < u0)) {
+                d2b = d2;
+                u0 = s;
+            }
+        });
+        if (dup) return -PFEM_ERR_DEGENERATE;
+        if (u0 < 0) continue;
+        int cur = u0, cnt = 0;
+        bool ok = true;
+        for (;;) {
+            if (cnt == KMAX) return -PFEM_ERR_CAPACITY;
+            nbrs[cnt++] = cur;
+            const int a = apex_search(B, pv, __ldg(B.q + cur), g);
+            if (a < 0) { ok = false; break; }
+            if (a == u0) break;
+            cur = a;
+        }
+        if (ok && cnt >= 3) return cnt;
+    }
+    return -PFEM_ERR_CAPACITY;
+}
+
+// Apex left of the directed edge u -> w, searching around u with growing regions.
+__device__ __forceinline__ int apex_of(const Bins &B, int u, int w, int R0)
+{
+    const uint2 pu = __ldg(B.q + u), pw = __ldg(B.q + w);
+    for (int R = R0; R <= B.rmax; ++R) {
+        const int a = apex_search(B, pu, pw, make_region(B, pu, R));
+        if (a >= 0) return a;
+    }
+    return -1;
+}
+
+// Locate fixed-point point p in the Delaunay triangulation: tri = counter-clockwise triangle
+// containing p (boundary included).  On success also returns the star of tri[0] in star0
+// (count n0) when tri[0] is the particle nearest to p, else n0 = 0.  Returns 0 or -PFEM_ERR_*.
+__device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tri[3], int *star0, int &n0)
+{
+    n0 = 0;
+    int v0 = -1;
+    for (int R = R0; R <= B.rmax && v0 < 0; ++R) {
+        const Region g = make_region(B, p, R);
+        long long d2b = 0x7fffffffffffffffLL;
+        int best = -1;
+        for_region(B, g, [&](int s) {
+            const int2 d = rel(__ldg(B.q + s), p);
+            const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
+            if (d2 < d2b || (d2 == d2b && s < best)) {
+                d2b = d2;
+                best = s;
+            }
+        });
+        const float clm = fminf(fminf(g.cl_lo_x, g.cl_hi_x), fminf(g.cl_lo_y, g.cl_hi_y));
+        if (best >= 0 && (float)d2b * 1.0001f < clm * clm) v0 = best;
+    }
+    if (v0 < 0) return -PFEM_ERR_CAPACITY;
+    const int cnt = star_of(B, v0, R0, star0);
+    if (cnt < 0) return cnt;
+    const uint2 q0 = __ldg(B.q + v0);
+    const int2 dp = rel(p, q0);
+    if (dp.x == 0 && dp.y == 0) {
+        tri[0] = v0; tri[1] = star0[0]; tri[2] = star0[1];
+        n0 = cnt;
+        return 0;
+    }
+    // sector of the fan around v0 that holds p: [st[j], st[j+1]) counter-clockwise
+    int j = -1;
+    int2 da = rel(__ldg(B.q + star0[cnt - 1]), q0);
+    for (int k = 0; k < cnt; ++k) {
+        const int2 dn = rel(__ldg(B.q + star0[k]), q0);
+        if (cross(da, dp) >= 0 && cross(dn, dp) < 0) { j = (k + cnt - 1) % cnt; break; }
+        da = dn;
+    }
+    if (j < 0) return -PFEM_ERR_DEGENERATE;
+    int e0 = star0[j], e1 = star0[(j + 1) % cnt];
+    {
+        const int2 a = rel(__ldg(B.q + e0), p), b = rel(__ldg(B.q + e1), p);
+        if (cross(a, b) >= 0) {                       // orient(e0, e1, p) >= 0
+            tri[0] = v0; tri[1] = e0; tri[2] = e1;
+            n0 = cnt;
+            return 0;
+        }
+    }
+    // visibility walk: p is strictly right of e0 -> e1; step into the triangle beyond.
+    for (int step = 0; step < 64; ++step) {
+        const int x = apex_of(B, e1, e0, R0);
+        if (x < 0) return -PFEM_ERR_CAPACITY;
+        const int2 a = rel(__ldg(B.q + e0), p), b = rel(__ldg(B.q + e1), p),
+                   c = rel(__ldg(B.q + x), p);
+        if (cross(a, c) < 0) { e1 = x; continue; }   // p strictly right of e0 -> x
+        if (cross(c, b) < 0) { e0 = x; continue; }   // p strictly right of x -> e1
+        tri[0] = e1; tri[1] = e0; tri[2] = x;
+        return 0;
+    }
+    return -PFEM_ERR_TIMEOUT;
+}
+
+}  // namespace pfem

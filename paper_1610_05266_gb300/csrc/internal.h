@@ -1,0 +1,48 @@
+// internal.h -- declarations shared by the translation units of libpfem (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/pfem.h"
+#include "common.cuh"
+
+namespace pfem {
+
+// Byte offsets of the workspace regions (the status word always sits at offset 0).
+struct WsLayout {
+    size_t status, count, key, rank, scan, bwd, total;
+};
+
+WsLayout ws_layout(int n, int nb, long long N, int C);
+size_t scan_scratch_ints(long long n);
+cudaError_t scan_exclusive(const int *in, int *out, long long n, int *scratch, cudaStream_t s);
+
+cudaError_t launch_build_cells(int nb, long long N, const void *pos, pfem_dtype pos_t,
+                               int *cell_start, int *perm, void *pos_sorted, uint32_t *q_sorted,
+                               const WsLayout &L, void *ws, cudaStream_t s);
+
+struct GeoArgs {
+    int n, nb;
+    long long N;
+    const void *pos_sorted;
+    pfem_dtype pos_t;
+    const uint32_t *q_sorted;
+    const int *cell_start;
+    int R0, rmax;
+};
+
+cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
+                       pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
+                       DevStatus *st, cudaStream_t s);
+cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
+                         void *w, pfem_dtype w_t, DevStatus *st, cudaStream_t s);
+cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_dtype val_t,
+                         const int *w_idx, const void *w, int K, pfem_dtype w_t, void *out,
+                         cudaStream_t s);
+cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st, cudaStream_t s);
+cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, int C,
+                       const void *mesh, void *vals, pfem_dtype val_t, cudaStream_t s);
+
+}  // namespace pfem

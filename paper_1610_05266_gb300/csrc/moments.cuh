@@ -1,0 +1,93 @@
+// moments.cuh -- the per-edge coefficient system of the quadratically consistent shape
+// functions (App. B, eqs. A0, A1, condquad; App. A: minimum-norm solution).
+//
+// For a Delaunay edge e = (nu, sigma) with stencil S_e, the coefficients A_mu (mu in S_e)
+// must satisfy sum A = 0, sum r A = 0 and sum r r^T A = -(1/2)(r_nu - r_sigma)(r_nu - r_sigma)^T
+// (eq. condquad rewritten with eqs. A0-A1, eq. A2_2).  In coordinates centred at the edge
+// midpoint and scaled by the edge length (the solution does not depend on the frame), with
+// p_mu = [1, x, y, x^2, xy, y^2], that is P A = b, P = [p_mu] (6 x k), and the minimum-norm
+// solution is A_mu = p_mu . y with M y = b, M = sum_mu p_mu p_mu^T (6 x 6, SPD for a stencil
+// not on one conic).  M is factorised by an unrolled Cholesky held in registers.
+#pragma once
+
+#include "common.cuh"
+
+namespace pfem {
+
+// packed lower triangle of a symmetric 6x6 matrix: (r, c), r >= c
+__host__ __device__ constexpr int tri_ix(int r, int c) { return r * (r + 1) / 2 + c; }
+
+template <typename S> struct Moment {
+    S m[21];
+
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 21; ++i) m[i] = S(0);
+    }
+
+    // M += p p^T for p = [1, x, y, x^2, xy, y^2]
+    __device__ __forceinline__ void add(S x, S y)
+    {
+        const S p[6] = {S(1), x, y, x * x, x * y, y * y};
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c) m[tri_ix(r, c)] = fma(p[r], p[c], m[tri_ix(r, c)]);
+    }
+
+    // In-place Cholesky M = L L^T; returns false when a pivot is not clearly positive
+    // (stencil numerically on one conic: the moment system is rank deficient).
+    __device__ __forceinline__ bool factor(S rel_tol)
+    {
+        S tr = S(0);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) tr += m[tri_ix(r, r)];
+        const S tol = rel_tol * tr;
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            S s = m[tri_ix(j, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fma(-m[tri_ix(j, k)], m[tri_ix(j, k)], s);
+            ok &= s > tol;
+            const S d = sqrt(s > tol ? s : tol);
+            const S inv = S(1) / d;
+            m[tri_ix(j, j)] = inv;               // store the reciprocal of the pivot
+#pragma unroll
+            for (int i = j + 1; i < 6; ++i) {
+                S t = m[tri_ix(i, j)];
+#pragma unroll
+                for (int k = 0; k < j; ++k) t = fma(-m[tri_ix(i, k)], m[tri_ix(j, k)], t);
+                m[tri_ix(i, j)] = t * inv;
+            }
+        }
+        return ok;
+    }
+
+    // Solve L L^T y = b with the factor from factor().
+    __device__ __forceinline__ void solve(const S b[6], S y[6]) const
+    {
+        S z[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            S t = b[r];
+#pragma unroll
+            for (int k = 0; k < r; ++k) t = fma(-m[tri_ix(r, k)], z[k], t);
+            z[r] = t * m[tri_ix(r, r)];
+        }
+#pragma unroll
+        for (int r = 5; r >= 0; --r) {
+            S t = z[r];
+#pragma unroll
+            for (int k = r + 1; k < 6; ++k) t = fma(-m[tri_ix(k, r)], y[k], t);
+            y[r] = t * m[tri_ix(r, r)];
+        }
+    }
+};
+
+template <typename S> struct SolveTol;
+template <> struct SolveTol<double> { static constexpr double v = 1e-13; };
+template <> struct SolveTol<float> { static constexpr float v = 1e-6f; };
+
+}  // namespace pfem

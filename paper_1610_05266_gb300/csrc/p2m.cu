@@ -1,0 +1,153 @@
+// p2m.cu -- launchers of the particle-to-mesh kernels (fused apply, explicit weights, apply
+// from explicit weights) and of the Delaunay-star diagnostic.
+#include "internal.h"
+#include "p2m.cuh"
+
+namespace pfem {
+
+static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
+{
+    P2MArgs a;
+    a.n = g.n;
+    a.B.q = (const uint2 *)g.q_sorted;
+    a.B.start = g.cell_start;
+    a.B.nb = g.nb;
+    a.B.rmax = g.rmax;
+    a.R0 = g.R0;
+    a.pos = g.pos_sorted;
+    a.perm = nullptr;
+    a.vals = nullptr;
+    a.C = 0;
+    a.out = nullptr;
+    a.w_idx = nullptr;
+    a.w = nullptr;
+    a.K = 0;
+    a.status = st;
+    return a;
+}
+
+static dim3 node_grid(int n) { return dim3((n + 15) / 16, (n + 7) / 8); }
+
+template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
+static cudaError_t go(const P2MArgs &a, cudaStream_t s)
+{
+    k_p2m<P, V, R, S, REF, SHAPE, W><<<node_grid(a.n), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
+                       pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
+                       DevStatus *st, cudaStream_t s)
+{
+    P2MArgs a = make_args(g, st);
+    a.perm = perm;
+    a.vals = vals;
+    a.C = C;
+    a.out = out;
+    const bool q = shape == PFEM_SHAPE_QUADRATIC;
+    if (val_t == PFEM_F64) {   // positions FP64, arithmetic FP64
+        if (!q) return go<double, double, double, double, false, 0, false>(a, s);
+        return go<double, double, double, double, false, 1, false>(a, s);
+    }
+    if (val_t == PFEM_F32) {   // positions FP32, arithmetic FP32
+        if (!q) return go<float, float, float, float, false, 0, false>(a, s);
+        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s);
+        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s);
+        return go<float, float, float, float, true, 1, false>(a, s);
+    }
+    if (!q) return go<float, __nv_bfloat16, float, float, false, 0, false>(a, s);
+    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s);
+    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s);
+    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s);
+}
+
+cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
+                         void *w, pfem_dtype w_t, DevStatus *st, cudaStream_t s)
+{
+    P2MArgs a = make_args(g, st);
+    a.K = K;
+    a.w_idx = w_idx;
+    a.w = w;
+    const bool q = shape == PFEM_SHAPE_QUADRATIC;
+    if (w_t == PFEM_F64) {
+        if (!q) return go<double, double, double, double, false, 0, true>(a, s);
+        return go<double, double, double, double, false, 1, true>(a, s);
+    }
+    if (!q) return go<float, float, float, float, false, 0, true>(a, s);
+    if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, true>(a, s);
+    if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, true>(a, s);
+    return go<float, float, float, float, true, 1, true>(a, s);
+}
+
+// alpha_i = sum_k w[i,k] alpha[w_idx[i,k]] (explicit-weight P2M)
+template <typename V, typename R>
+__global__ void __launch_bounds__(256) k_apply(long long nodes, int K, const int *__restrict__ w_idx,
+                                               const R *__restrict__ w, const int *__restrict__ perm,
+                                               int C, const V *__restrict__ vals, V *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        R acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = R(0);
+        for (int k = 0; k < K; ++k) {
+            const int s = __ldg(w_idx + i * K + k);
+            if (s < 0) break;
+            const R wk = __ldg(w + i * K + k);
+            R v[8];
+            load_vals<V, R>(vals, perm, s, C, v);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < C) acc[c] = fma(wk, v[c], acc[c]);
+        }
+        store_vals<V, R>(out, i, C, acc);
+    }
+}
+
+cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_dtype val_t,
+                         const int *w_idx, const void *w, int K, pfem_dtype w_t, void *out,
+                         cudaStream_t s)
+{
+    const long long nodes = (long long)n * n;
+    long long blocks = (nodes + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (val_t == PFEM_F64 && w_t == PFEM_F64)
+        k_apply<double, double><<<(unsigned)blocks, 256, 0, s>>>(
+            nodes, K, w_idx, (const double *)w, perm, C, (const double *)vals, (double *)out);
+    else if (val_t == PFEM_F32 && w_t == PFEM_F32)
+        k_apply<float, float><<<(unsigned)blocks, 256, 0, s>>>(
+            nodes, K, w_idx, (const float *)w, perm, C, (const float *)vals, (float *)out);
+    else if (val_t == PFEM_BF16 && w_t == PFEM_F32)
+        k_apply<__nv_bfloat16, float><<<(unsigned)blocks, 256, 0, s>>>(
+            nodes, K, w_idx, (const float *)w, perm, C, (const __nv_bfloat16 *)vals,
+            (__nv_bfloat16 *)out);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(128) k_stars(Bins B, int R0, long long N, int *nbrs, int *counts,
+                                               DevStatus *st)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        int loc[KMAX];
+        const int c = star_of(B, (int)v, R0, loc);
+        if (c < 0) record_error(st, -c, v);
+        const int cnt = c < 0 ? 0 : c;
+        for (int k = 0; k < KMAX; ++k) nbrs[v * KMAX + k] = k < cnt ? loc[k] : -1;
+        counts[v] = cnt;
+    }
+}
+
+cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st, cudaStream_t s)
+{
+    P2MArgs a = make_args(g, st);
+    long long blocks = (g.N + 127) / 128;
+    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    if (blocks < 1) blocks = 1;
+    k_stars<<<(unsigned)blocks, 128, 0, s>>>(a.B, g.R0, g.N, nbrs, counts, st);
+    return cudaGetLastError();
+}
+
+}  // namespace pfem

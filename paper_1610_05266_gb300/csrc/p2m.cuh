@@ -1,0 +1,312 @@
+// p2m.cuh -- per-node particle-to-mesh projection (Sec. 2.2 eq. p2m) with linear FE or
+// quadratically consistent shape functions (App. B eq. phiquad), one thread per mesh node.
+//
+// For node r_i in the particle Delaunay triangle T = (a, b, c) with barycentrics lambda, the
+// only nonzero linear shape functions are lambda_a, lambda_b, lambda_c, and eq. (phiquad)
+// sums A_{mu nu sigma} phi_nu phi_sigma over ordered pairs of distinct, adjacent nu, sigma --
+// the three edges of T, each twice.  So
+//     w_{i mu} = lambda_mu [mu in T] + sum_{e=(nu,sigma) in T} 2 lambda_nu lambda_sigma A_{mu e},
+// and alpha_i = sum_mu w_{i mu} alpha_mu for every field component in one pass.
+#pragma once
+
+#include "geom.cuh"
+#include "moments.cuh"
+
+namespace pfem {
+
+struct P2MArgs {
+    int n;                      // mesh nodes per side (image row/column included)
+    Bins B;
+    int R0;                     // first search radius in bins
+    const void *pos;            // [N,2] positions in slot order
+    const int *perm;            // slot -> original index, or nullptr (values in slot order)
+    const void *vals;           // [N,C]
+    int C;
+    void *out;                  // [n,n,C] mesh values (apply mode)
+    int *w_idx;                 // [n*n, K] (weights mode)
+    void *w;                    // [n*n, K]
+    int K;
+    DevStatus *status;
+};
+
+// Node position and minimal-image offsets in the compute precision R.
+template <typename P, typename R> struct NodePos;
+
+template <> struct NodePos<double, double> {
+    double x, y;
+    __device__ __forceinline__ void init(int Iu, int Ju, int nc)
+    {
+        x = (double)Iu / (double)nc;
+        y = (double)Ju / (double)nc;
+    }
+    __device__ __forceinline__ void off(const void *pos, int s, double &dx, double &dy) const
+    {
+        double px, py;
+        load_pos((const double *)pos, s, px, py);
+        dx = wrap1(px - x);
+        dy = wrap1(py - y);
+    }
+};
+
+// FP32 offsets: the node coordinate I/nc is carried as hi + lo, so that an offset is accurate
+// to FP32 relative precision (px - hi is exact for nearby values, and wraps exactly).
+template <> struct NodePos<float, float> {
+    float xh, xl, yh, yl;
+    __device__ __forceinline__ void init(int Iu, int Ju, int nc)
+    {
+        const float f = (float)nc;
+        xh = (float)Iu / f;
+        xl = fmaf(-xh, f, (float)Iu) / f;
+        yh = (float)Ju / f;
+        yl = fmaf(-yh, f, (float)Ju) / f;
+    }
+    __device__ __forceinline__ void off(const void *pos, int s, float &dx, float &dy) const
+    {
+        float px, py;
+        load_pos((const float *)pos, s, px, py);
+        dx = wrap1(px - xh) - xl;
+        dy = wrap1(py - yh) - yl;
+    }
+};
+
+template <typename V, typename R>
+__device__ __forceinline__ void load_vals(const V *vals, const int *perm, int s, int C, R out[8])
+{
+    const long long idx = perm ? (long long)__ldg(perm + s) : (long long)s;
+    const V *p = vals + idx * C;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c < C) out[c] = load_val<V, R>(p + c);
+}
+
+template <>
+__device__ __forceinline__ void load_vals<float, float>(const float *vals, const int *perm, int s,
+                                                        int C, float out[8])
+{
+    const long long idx = perm ? (long long)__ldg(perm + s) : (long long)s;
+    if (C == 4 && (reinterpret_cast<uintptr_t>(vals) & 15) == 0) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(vals) + idx);
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+        return;
+    }
+    const float *p = vals + idx * C;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c < C) out[c] = __ldg(p + c);
+}
+
+template <typename V, typename R>
+__device__ __forceinline__ void store_vals(V *out, long long node, int C, const R acc[8])
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c < C) store_val<V, R>(out + node * C + c, acc[c]);
+}
+
+template <>
+__device__ __forceinline__ void store_vals<float, float>(float *out, long long node, int C,
+                                                        const float acc[8])
+{
+    if (C == 4 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        reinterpret_cast<float4 *>(out)[node] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (c < C) out[node * C + c] = acc[c];
+}
+
+__device__ __forceinline__ bool in_list(const int *lst, int n, int x)
+{
+    for (int i = 0; i < n; ++i)
+        if (lst[i] == x) return true;
+    return false;
+}
+
+// Coefficients A_{mu e} of edge e = (nu, sg) over S_e = {nu} + star(nu) + star(sg) (each
+// particle once; sg is in star(nu), nu in star(sg)).  Calls emit(slot, coef * A_mu) for every
+// stencil member.  S is the solve precision; REFINE adds one refinement step with an FP64
+// residual.  Returns false when the moment matrix is numerically singular.
+template <typename P, typename R, typename S, bool REFINE, typename Emit>
+__device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, R> &np, int nu,
+                                             int sg, const int *st_nu, int n_nu,
+                                             const int *st_sg, int n_sg, R coef, Emit &&emit)
+{
+    R rnx, rny, rsx, rsy;
+    np.off(a.pos, nu, rnx, rny);
+    np.off(a.pos, sg, rsx, rsy);
+    const S mx = (S(rnx) + S(rsx)) * S(0.5), my = (S(rny) + S(rsy)) * S(0.5);
+    const S ex = S(rnx) - S(rsx), ey = S(rny) - S(rsy);
+    const S inv = S(1) / sqrt(ex * ex + ey * ey);
+
+    // visit every stencil member once: nu, star(nu), then star(sg) minus {nu} + star(nu)
+    auto for_stencil = [&](auto &&f) {
+        f(nu);
+        for (int i = 0; i < n_nu; ++i) f(st_nu[i]);
+        for (int j = 0; j < n_sg; ++j) {
+            const int m = st_sg[j];
+            if (m == nu || in_list(st_nu, n_nu, m)) continue;
+            f(m);
+        }
+    };
+    auto coords = [&](int s, S &x, S &y) {
+        R dx, dy;
+        np.off(a.pos, s, dx, dy);
+        x = (S(dx) - mx) * inv;
+        y = (S(dy) - my) * inv;
+    };
+
+    Moment<S> M;
+    M.zero();
+    for_stencil([&](int s) {
+        S x, y;
+        coords(s, x, y);
+        M.add(x, y);
+    });
+    if (!M.factor(SolveTol<S>::v)) return false;
+    const S tx = ex * inv, ty = ey * inv;
+    const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
+    S y[6];
+    M.solve(b, y);
+    if (REFINE) {
+        // r = b - (sum p p^T) y with p from the same FP32 coordinates, accumulated in FP64
+        double r[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) r[i] = (double)b[i];
+        for_stencil([&](int s) {
+            S x, y2;
+            coords(s, x, y2);
+            const double X = x, Y = y2;
+            const double p[6] = {1.0, X, Y, X * X, X * Y, Y * Y};
+            double t = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t = fma(p[i], (double)y[i], t);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) r[i] = fma(-p[i], t, r[i]);
+        });
+        S rs[6], dy[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) rs[i] = (S)r[i];
+        M.solve(rs, dy);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] += dy[i];
+    }
+    for_stencil([&](int s) {
+        S x, y2;
+        coords(s, x, y2);
+        const S A = y[0] + x * y[1] + y2 * y[2] + x * x * y[3] + x * y2 * y[4] + y2 * y2 * y[5];
+        emit(s, coef * R(A));
+    });
+    return true;
+}
+
+template <typename V> __device__ __forceinline__ V nan_of();
+template <> __device__ __forceinline__ float nan_of<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double nan_of<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// One mesh node.  WEIGHTS = false: write alpha_i for all C components; true: write the
+// node's distinct (slot, weight) pairs.
+template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS>
+__device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
+{
+    const int nc = a.n - 1;
+    const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+    const long long node = (long long)J * a.n + I;
+    const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+    int tri[3];
+    int stars[3][KMAX];
+    int ns[3] = {0, 0, 0};
+    int st = locate(a.B, qn, a.R0, tri, stars[0], ns[0]);
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && st == 0) {
+        for (int e = 0; e < 3 && st == 0; ++e)
+            if (ns[e] == 0) {
+                const int c = star_of(a.B, tri[e], a.R0, stars[e]);
+                if (c < 0) st = c;
+                else ns[e] = c;
+            }
+    }
+    NodePos<P, R> np;
+    np.init(Iu, Ju, nc);
+    R lam[3] = {R(0), R(0), R(0)};
+    if (st == 0) {
+        R d[3][2];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
+        const R area2 = (d[1][0] - d[0][0]) * (d[2][1] - d[0][1]) - (d[1][1] - d[0][1]) * (d[2][0] - d[0][0]);
+        lam[0] = (d[1][0] * d[2][1] - d[1][1] * d[2][0]) / area2;
+        lam[1] = (d[2][0] * d[0][1] - d[2][1] * d[0][0]) / area2;
+        lam[2] = (d[0][0] * d[1][1] - d[0][1] * d[1][0]) / area2;
+    }
+
+    if (!WEIGHTS) {
+        R acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = R(0);
+        auto emit = [&](int s, R wgt) {
+            R v[8];
+            load_vals<V, R>((const V *)a.vals, a.perm, s, a.C, v);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < a.C) acc[c] = fma(wgt, v[c], acc[c]);
+        };
+        if (st == 0) {
+            for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
+            if (SHAPE == PFEM_SHAPE_QUADRATIC)
+                for (int e = 0; e < 3 && st == 0; ++e) {
+                    const int f = e == 2 ? 0 : e + 1;
+                    if (!edge_weights<P, R, S, REFINE>(a, np, tri[e], tri[f], stars[e], ns[e],
+                                                       stars[f], ns[f], R(2) * lam[e] * lam[f], emit))
+                        st = -PFEM_ERR_DEGENERATE;
+                }
+        }
+        if (st != 0) {
+            record_error(a.status, -st, node);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+        }
+        store_vals<V, R>((V *)a.out, node, a.C, acc);
+    } else {
+        int idx[PFEM_KW_MAX];
+        R wl[PFEM_KW_MAX];
+        int cnt = 0;
+        bool over = false;
+        auto emit = [&](int s, R wgt) {
+            for (int i = 0; i < cnt; ++i)
+                if (idx[i] == s) { wl[i] += wgt; return; }
+            if (cnt < a.K) { idx[cnt] = s; wl[cnt] = wgt; ++cnt; }
+            else over = true;
+        };
+        if (st == 0) {
+            for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
+            if (SHAPE == PFEM_SHAPE_QUADRATIC)
+                for (int e = 0; e < 3 && st == 0; ++e) {
+                    const int f = e == 2 ? 0 : e + 1;
+                    if (!edge_weights<P, R, S, REFINE>(a, np, tri[e], tri[f], stars[e], ns[e],
+                                                       stars[f], ns[f], R(2) * lam[e] * lam[f], emit))
+                        st = -PFEM_ERR_DEGENERATE;
+                }
+            if (over && st == 0) st = -PFEM_ERR_CAPACITY;
+        }
+        if (st != 0) {
+            record_error(a.status, -st, node);
+            cnt = 0;
+        }
+        int *oi = a.w_idx + node * a.K;
+        R *ow = (R *)a.w + node * a.K;
+        for (int k = 0; k < a.K; ++k) {
+            oi[k] = k < cnt ? idx[k] : -1;
+            ow[k] = k < cnt ? wl[k] : R(0);
+        }
+    }
+}
+
+template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS>
+__global__ void __launch_bounds__(128) k_p2m(P2MArgs a)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
+    p2m_node<P, V, R, S, REFINE, SHAPE, WEIGHTS>(a, I, J);
+}
+
+}  // namespace pfem

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs.  Cell lists and Delaunay stars must match bit for bit (ties included); FP64 values
+within 1e-12 relative (inf-norm over the output, relative to its largest magnitude);
+reduced-precision variants report their error against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import generators as G
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_05266_gb300 as P
+    return P
+
+
+def relerr(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def cyclic_canon(seq):
+    seq = list(seq)
+    k = int(np.argmin(seq))
+    return seq[k:] + seq[:k]
+
+
+def gpu_setup(P, pr, dtype=torch.float64, nb=None):
+    dev = torch.device("cuda")
+    pos = torch.tensor(pr.pos, dtype=dtype, device=dev)
+    proj = P.Projector(pr.n, pr.N, C=pr.C, nb=nb, pos_dtype=dtype, device=dev)
+    proj.build(pos)
+    return proj, pos
+
+
+def test_cell_list_bit_exact(P):
+    pr = G.config_tiny()
+    for dtype in (torch.float64, torch.float32):
+        proj, _ = gpu_setup(P, pr, dtype)
+        pos64 = pr.pos if dtype == torch.float64 else pr.pos.astype(np.float32).astype(np.float64)
+        ref = O.build_cells(proj.nb + 1, pos64)
+        c = proj.cells
+        assert np.array_equal(c.cell_start.cpu().numpy(), ref.cell_start)
+        assert np.array_equal(c.perm.cpu().numpy(), ref.perm)
+        assert np.array_equal(c.q_sorted.cpu().numpy().view(np.uint32), ref.qs)
+        assert np.array_equal(c.pos_sorted.cpu().numpy().astype(np.float64), pos64[ref.perm])
+
+
+def test_cell_list_ragged_and_empty(P):
+    dev = torch.device("cuda")
+    for N, nb in ((0, 8), (1, 8), (1001, 13), (70000, 100)):
+        pos = G.uniform01(G.SEED_BASE + N, 2 * max(N, 1))[: 2 * N].reshape(N, 2)
+        proj = P.Projector(33, N, nb=nb, pos_dtype=torch.float64, device=dev)
+        proj.build(torch.tensor(pos, device=dev).reshape(N, 2))
+        torch.cuda.synchronize()
+        ref = O.build_cells(nb + 1, pos)
+        assert np.array_equal(proj.cells.cell_start.cpu().numpy(), ref.cell_start)
+        if N:
+            assert np.array_equal(proj.cells.perm.cpu().numpy()[:N], ref.perm)
+
+
+@pytest.mark.parametrize("jitter", [0.25, 0.0])
+def test_delaunay_stars_bit_exact(P, jitter):
+    """Every particle's counter-clockwise star equals the oracle's (an unjittered lattice is
+    all cocircular squares: the tie-break must agree too)."""
+    M = 64
+    pos = G.jittered_lattice(M, jitter, G.SEED_BASE + 1)
+    pr = G.Problem("s", 33, M, jitter, 0, pos, np.zeros((M * M, 1)))
+    proj, _ = gpu_setup(P, pr)
+    nbrs, counts = proj.stars()
+    proj.check("stars")
+    nbrs, counts = nbrs.cpu().numpy(), counts.cpu().numpy()
+    perm = proj.cells.perm.cpu().numpy()
+    ref_cells = O.build_cells(pr.n, pos)
+    assert counts.sum() == 6 * pr.N
+    for s in range(pr.N):
+        mine = perm[nbrs[s, : counts[s]]]
+        ref = O.star(ref_cells, int(perm[s]))
+        assert cyclic_canon(mine) == cyclic_canon(ref), s
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_p2m_fp64_tiny(P, shape):
+    pr = G.config_tiny()
+    proj, _ = gpu_setup(P, pr)
+    vals = torch.tensor(pr.vals, device="cuda")
+    mesh = proj.p2m(vals, shape=shape)
+    proj.check("p2m")
+    ref = O.p2m(pr.n, pr.pos, pr.vals, shape=shape, nthreads=8)
+    assert relerr(mesh.cpu().numpy(), ref) <= TOL64
+    again = proj.p2m(vals, shape=shape)
+    assert torch.equal(mesh, again)                        # deterministic, no atomics
+    m = mesh.cpu().numpy()
+    assert np.array_equal(m[-1], m[0]) and np.array_equal(m[:, -1], m[:, 0])  # image copies
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_shape_weights_fp64_tiny(P, shape):
+    """Explicit weights: the set of particles per node is bit-exact, weights within 1e-12."""
+    pr = G.config_tiny()
+    proj, _ = gpu_setup(P, pr)
+    w_idx, w = proj.shape_weights(shape=shape, K=32)
+    proj.check("shape")
+    w_idx, w = w_idx.cpu().numpy(), w.cpu().numpy()
+    perm = proj.cells.perm.cpu().numpy()
+    cells = O.build_cells(pr.n, pr.pos)
+    for node in range(pr.n * pr.n):
+        J, I = divmod(node, pr.n)
+        k = w_idx[node] >= 0
+        mine = dict(zip(perm[w_idx[node][k]].tolist(), w[node][k].tolist()))
+        idx, ww, _, _ = O.node_weights(cells, I, J, shape)
+        ref = dict(zip(idx.tolist(), ww.tolist()))
+        assert set(mine) == set(ref), node
+        assert max(abs(mine[i] - ref[i]) for i in ref) <= TOL64
+
+
+def test_apply_explicit_weights_matches_fused(P):
+    pr = G.config_tiny()
+    proj, _ = gpu_setup(P, pr)
+    vals = torch.tensor(pr.vals, device="cuda")
+    fused = proj.p2m(vals, shape=1)
+    wts = proj.shape_weights(shape=1, K=32)
+    applied = proj.p2m(vals, weights=wts)
+    proj.check()
+    assert relerr(applied.cpu().numpy(), fused.cpu().numpy()) <= 1e-14
+
+
+def test_m2p_fp64_and_reduced(P):
+    pr = G.config_tiny()
+    rng = np.random.default_rng(5)
+    mesh = rng.standard_normal((pr.n, pr.n, 3))
+    ref = O.m2p(pr.n, pr.pos, mesh)
+    proj, pos = gpu_setup(P, pr)
+    out = proj.m2p(pos, torch.tensor(mesh, device="cuda"))
+    assert relerr(out.cpu().numpy(), ref) <= TOL64
+    pos32 = pos.float()
+    ref32 = O.m2p(pr.n, pr.pos.astype(np.float32).astype(np.float64), mesh)
+    e32 = relerr(proj.m2p(pos32, torch.tensor(mesh, device="cuda", dtype=torch.float32)).cpu().numpy(), ref32)
+    ebf = relerr(proj.m2p(pos32, torch.tensor(mesh, device="cuda", dtype=torch.bfloat16)).float().cpu().numpy(), ref32)
+    print(f"M2P error vs FP64 oracle: fp32 {e32:.2e}, bf16 {ebf:.2e}")
+    assert e32 < 1e-6 and ebf < 2e-2
+
+
+def test_m2p_ragged_sizes(P):
+    for n, N in ((9, 1), (17, 333), (50, 4097)):
+        pos = G.uniform01(G.SEED_BASE + n, 2 * N).reshape(N, 2) * 3 - 1   # outside [0,1) too
+        mesh = np.random.default_rng(n).standard_normal((n, n, 5))
+        proj = P.Projector(n, max(N, 3), pos_dtype=torch.float64)
+        out = proj.m2p(torch.tensor(pos, device="cuda"), torch.tensor(mesh, device="cuda"))
+        assert relerr(out.cpu().numpy(), O.m2p(n, pos, mesh)) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_p2m_degenerate_lattice(P, shape):
+    """Unjittered lattice: nodes sit on cocircular squares' diagonals; values still match."""
+    n, M = 33, 64
+    pos = G.jittered_lattice(M, 0.0, 0)
+    vals = G.taylor_green(pos)
+    pr = G.Problem("lat", n, M, 0.0, 0, pos, vals)
+    proj, _ = gpu_setup(P, pr)
+    mesh = proj.p2m(torch.tensor(vals, device="cuda"), shape=shape)
+    proj.check()
+    assert relerr(mesh.cpu().numpy(), O.p2m(n, pos, vals, shape=shape, nthreads=8)) <= TOL64
+
+
+def test_p2m_ragged_mesh_and_ratios(P):
+    """Mesh sizes that leave partial node tiles, and h/H = 1, 1/2, 1/4."""
+    for n, M in ((26, 25), (41, 80), (18, 68)):
+        pos = G.jittered_lattice(M, 0.3, G.SEED_BASE + n)
+        vals = G.taylor_green(pos, k=2)
+        pr = G.Problem("r", n, M, 0.3, 0, pos, vals)
+        proj, _ = gpu_setup(P, pr)
+        for shape in (0, 1):
+            mesh = proj.p2m(torch.tensor(vals, device="cuda"), shape=shape)
+            proj.check()
+            assert relerr(mesh.cpu().numpy(), O.p2m(n, pos, vals, shape=shape, nthreads=8)) <= TOL64
+
+
+def test_duplicate_particles_flagged(P):
+    pos = G.jittered_lattice(32, 0.25, 3)
+    pos[100] = pos[200]
+    pr = G.Problem("d", 17, 32, 0.25, 0, pos, np.ones((1024, 1)))
+    proj, _ = gpu_setup(P, pr)
+    proj.p2m(torch.ones((1024, 1), dtype=torch.float64, device="cuda"), shape=1)
+    code, _ = proj.status()
+    assert code == 5
+
+
+def test_reduced_precision_errors_tiny(P):
+    """FP32 / BF16-storage variants against the FP64 oracle (errors are stated, loosely
+    bounded)."""
+    pr = G.config_tiny()
+    pos32 = pr.pos.astype(np.float32)
+    ref = O.p2m(pr.n, pos32.astype(np.float64), pr.vals, shape=1, nthreads=8)
+    proj, _ = gpu_setup(P, G.Problem("t", pr.n, pr.M, pr.a, 0, pos32.astype(np.float64), pr.vals),
+                        torch.float32)
+    errs = {}
+    for vt in (torch.float32, torch.bfloat16):
+        v = torch.tensor(pr.vals, device="cuda").to(vt)
+        for solve, name in ((P.PFEM_SOLVE_F64, "f64"), (P.PFEM_SOLVE_F32, "f32"),
+                            (P.PFEM_SOLVE_F32_REFINED, "f32+ref")):
+            m = proj.p2m(v, shape=1, solve=solve)
+            proj.check()
+            errs[(str(vt), name)] = relerr(m.float().cpu().numpy(), ref)
+    print("P2M error vs FP64 oracle:", {k: f"{e:.2e}" for k, e in errs.items()})
+    for (vt, _), e in errs.items():
+        assert e < (1e-5 if "float32" in vt else 2e-2)
