@@ -78,6 +78,10 @@ typedef enum { PFEM_BACKWARD_RECOMPUTE = 0, PFEM_BACKWARD_CHECKPOINT = 1 } pfem_
 /* Version of this ABI. */
 int pfem_abi_version(void);
 
+/* Number of kernels this library has launched in this process (all devices, all streams);
+ * lets a caller count the launches inside a timed region.  No paper counterpart. */
+uint64_t pfem_launch_count(void);
+
 /* Human-readable name of a status code. */
 const char *pfem_status_string(pfem_status s);
 

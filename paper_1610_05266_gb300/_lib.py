@@ -29,6 +29,7 @@ STATUS = {0: "PFEM_OK", 1: "PFEM_ERR_INVALID_ARG", 2: "PFEM_ERR_CUDA", 3: "PFEM_
 _i32, _i64, _sz, _p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
 SIGNATURES = {
     "pfem_abi_version": (ctypes.c_int, []),
+    "pfem_launch_count": (ctypes.c_uint64, []),
     "pfem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pfem_default_bins": (_i32, [_i32, _i64]),
     "pfem_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),

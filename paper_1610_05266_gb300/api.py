@@ -21,6 +21,10 @@ def pfem_abi_version() -> int:
     return L.load().pfem_abi_version()
 
 
+def pfem_launch_count() -> int:
+    return int(L.load().pfem_launch_count())
+
+
 def pfem_default_bins(n: int, N: int) -> int:
     return int(L.load().pfem_default_bins(n, N))
 

@@ -7,7 +7,12 @@
 
 using namespace pfem;
 
+#include <atomic>
+
 namespace pfem {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -76,6 +81,8 @@ static bool make_geo(int32_t n, int32_t nb, int64_t N, const void *pos_sorted, p
 extern "C" {
 
 int pfem_abi_version(void) { return 1; }
+
+uint64_t pfem_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 const char *pfem_status_string(pfem_status s)
 {

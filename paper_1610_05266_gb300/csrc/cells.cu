@@ -135,10 +135,12 @@ cudaError_t scan_exclusive(const int *in, int *out, long long n, int *scratch, c
     int *sums = scratch;
     int *sums_scan = scratch + tiles + 32;
     k_scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    count_launch();
     if (tiles > 1) {
         cudaError_t e = scan_exclusive(sums, sums_scan, tiles, sums_scan + tiles + 32, s);
         if (e != cudaSuccess) return e;
         k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sums_scan);
+        count_launch();
     }
     return cudaGetLastError();
 }
@@ -163,13 +165,17 @@ static cudaError_t build_cells_t(int nb, long long N, const P *pos, int *cell_st
     int *scr = (int *)(ws + L.scan);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(nbins + 1), s);
     if (e != cudaSuccess) return e;
-    if (N > 0) k_bin<P><<<grid_for(N, 256), 256, 0, s>>>(pos, N, nb, key, rank, count);
+    if (N > 0) {
+        k_bin<P><<<grid_for(N, 256), 256, 0, s>>>(pos, N, nb, key, rank, count);
+        count_launch();
+    }
     e = scan_exclusive(count, cell_start, nbins + 1, scr, s);
     if (e != cudaSuccess) return e;
     if (N > 0) {
         k_scatter<<<grid_for(N, 256), 256, 0, s>>>(N, key, rank, cell_start, perm);
         k_sort_bins<<<grid_for(nbins, 128), 128, 0, s>>>(nbins, cell_start, perm);
         k_gather<P><<<grid_for(N, 256), 256, 0, s>>>(N, pos, perm, pos_sorted, q_sorted);
+        count_launch(3);
     }
     return cudaGetLastError();
 }

@@ -10,6 +10,9 @@
 
 namespace pfem {
 
+// Launch counter behind pfem_launch_count(); every kernel launch site calls count_launch().
+void count_launch(unsigned k = 1);
+
 // Byte offsets of the workspace regions (the status word always sits at offset 0).
 struct WsLayout {
     size_t status, count, key, rank, scan, bwd, total;

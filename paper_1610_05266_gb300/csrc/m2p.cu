@@ -73,6 +73,7 @@ static cudaError_t m2p_t(int n, long long N, const void *pos, int C, const void 
     else
         k_m2p<P, V, R, 0><<<(unsigned)blocks, 256, 0, s>>>(n, N, (const P *)pos, C,
                                                           (const V *)mesh, (V *)vals);
+    count_launch();
     return cudaGetLastError();
 }
 

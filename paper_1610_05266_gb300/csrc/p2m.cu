@@ -32,6 +32,7 @@ template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, b
 static cudaError_t go(const P2MArgs &a, cudaStream_t s)
 {
     k_p2m<P, V, R, S, REF, SHAPE, W><<<node_grid(a.n), 128, 0, s>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -123,6 +124,7 @@ cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_d
             (__nv_bfloat16 *)out);
     else
         return cudaErrorInvalidValue;
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -147,6 +149,7 @@ cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st
     if (blocks > 152LL * 32) blocks = 152LL * 32;
     if (blocks < 1) blocks = 1;
     k_stars<<<(unsigned)blocks, 128, 0, s>>>(a.B, g.R0, g.N, nbrs, counts, st);
+    count_launch();
     return cudaGetLastError();
 }
 
