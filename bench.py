@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the particle <-> fixed-mesh projection round trip on one GB300.
+
+Workload: 1025 x 1025 periodic mesh (H = 1/1024), 2048 x 2048 jittered particles (h = H/2,
+jitter 0.25 h), four FP32 channels (Taylor-Green u, v, p and a Zalesak slotted-disk
+indicator).  One step = bin the particles (stable counting sort) -> quadratic P2M with the
+shape functions built on the fly -> linear-FE M2P, all through the C ABI.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mparticles/s for P2M+M2P round trip; %HBM peak; max rel err vs FP64 oracle"
+UNIT = "Mparticles/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# FP32 arithmetic of the quadratic P2M per node ("roofline"): barycentrics
+# (30) + 3 edges x (244 + 77 k) with mean stencil size k = 10, + linear apply (24), C = 4.
+FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * 10) + 24
+FP32_LANES = 152 * 128
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)                  # let the sampler come up before the timed region
+        except Exception:
+            self.proc = None
+
+    def mark(self, which: str):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        import datetime
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                rows.append((ts, parts[1:]))
+        if not rows:
+            return None
+        t0, t1 = getattr(self, "t_start", 0.0), getattr(self, "t_end", 1e300)
+        inside = [r for t, r in rows if t0 - 0.05 <= t <= t1 + 0.05]
+        if not inside:   # timed region shorter than one sampling period: nearest samples
+            inside = [min(rows, key=lambda x: abs(x[0] - 0.5 * (t0 + t1)))[1]]
+        num = lambda v: float(v) if v.replace(".", "").isdigit() else None
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        mx = [num(r[2]) for r in inside if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside), "timed_s": t1 - t0}
+
+
+def oracle_baseline(pr, node_sample: int, particle_sample: int, threads: int):
+    """Time the FP64 oracle on a bounded sample of the workload; scale to the whole job."""
+    import oracle as O
+    n, N = pr.n, pr.N
+    pos = np.ascontiguousarray(pr.pos.astype(np.float32).astype(np.float64))
+    vals = np.ascontiguousarray(pr.vals)
+    t0 = time.perf_counter()
+    O.build_cells(n, pos)
+    t_cells = time.perf_counter() - t0
+    nn = n * n
+    b = (nn // 2) - node_sample // 2
+    t0 = time.perf_counter()
+    O.p2m(n, pos, vals, shape=1, nthreads=threads, node_range=(b, b + node_sample))
+    t_p2m = time.perf_counter() - t0 - t_cells
+    mesh = np.zeros((n, n, vals.shape[1]))
+    t0 = time.perf_counter()
+    O.m2p(n, pos[:particle_sample], mesh)
+    t_m2p = time.perf_counter() - t0
+    full = t_cells + max(t_p2m, 0.0) * nn / node_sample + t_m2p * N / particle_sample
+    work = t_cells + max(t_p2m, 0.0) + t_m2p
+    return full, work, {"cells_s": t_cells, "p2m_nodes": node_sample, "p2m_s": t_p2m,
+                        "m2p_particles": particle_sample, "m2p_s": t_m2p}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from workloads import config_large
+    pr = config_large()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_baseline(pr, 2048, 1 << 16, threads)
+    times, works, last = [], [], None
+    for _ in range(args.steps):
+        full, work, last = oracle_baseline(pr, 2048, 1 << 16, threads)
+        times.append(full)
+        works.append(work)
+    t = float(np.mean(times))
+    value = pr.N / t / 1e6
+    sample = (f"per step: oracle bins of all {pr.N} particles, quadratic P2M on 2048 of "
+              f"{pr.n * pr.n} nodes ({threads} OpenMP threads), M2P on 65536 particles; "
+              f"scaled to the full round trip")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": pr.name, "mesh_nodes": f"{pr.n}x{pr.n}",
+                      "particles": f"{pr.M}x{pr.M}", "channels": pr.C},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample, "cpu_seconds_per_step": float(np.mean(works)),
+                            "breakdown": last},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1610_05266_gb300 as P
+    from workloads import config_large
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load()
+    pr = config_large()
+    n, N, C = pr.n, pr.N, pr.C
+    nn = n * n
+    pos = torch.tensor(pr.pos, dtype=torch.float32, device=dev)
+    vals = torch.tensor(pr.vals, dtype=torch.float32, device=dev)
+    proj = P.Projector(n, N, C=C, pos_dtype=torch.float32, device=dev)
+    mesh = torch.empty((n, n, C), dtype=torch.float32, device=dev)
+    back = torch.empty((N, C), dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    solve = {"f32": P.PFEM_SOLVE_F32, "f32ref": P.PFEM_SOLVE_F32_REFINED, "f64": P.PFEM_SOLVE_F64}[args.solve]
+    stream = torch.cuda.current_stream()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    def step(rec=None):
+        if rec is not None:
+            rec[0].record(stream)
+        proj.build(pos)
+        if rec is not None:
+            rec[1].record(stream)
+        proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=solve, out=mesh)
+        if rec is not None:
+            rec[2].record(stream)
+        proj.m2p(pos, mesh, out=back)
+        if rec is not None:
+            rec[3].record(stream)
+
+    for _ in range(max(args.warmup, 3) if not args.profile else args.warmup):
+        step()
+    torch.cuda.synchronize()
+    proj.check("warm-up")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    recs = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    l0 = P.pfem_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.mark("t_start")
+    for k in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps (outside the events)
+        step(recs[k])
+    torch.cuda.synchronize()
+    clocks.mark("t_end")
+    barrier(world)
+    launches = P.pfem_launch_count() - l0
+    clk = clocks.stop()
+    proj.check("timed steps")
+    step_ms = [r[0].elapsed_time(r[3]) for r in recs]
+    cells_ms = [r[0].elapsed_time(r[1]) for r in recs]
+    p2m_ms = [r[1].elapsed_time(r[2]) for r in recs]
+    m2p_ms = [r[2].elapsed_time(r[3]) for r in recs]
+    t_step = max_over_ranks(float(np.sum(step_ms)) / args.steps, world)
+    value = world * N / (t_step * 1e-3) / 1e6
+
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    t_p2m = float(np.mean(p2m_ms)) * 1e-3
+    t_m2p = float(np.mean(m2p_ms)) * 1e-3
+    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = FP32_LANES * 2 * 2070.0e6 / 1e12            # TFLOP/s at the maximum SM clock
+    p2m_flops = FLOP_PER_NODE_Q * nn
+    # algorithmic bytes of the round trip: P2M reads pos + C vals per particle and writes C
+    # per node; M2P reads pos per particle, C per node, writes C per particle (FP32)
+    rt_bytes = N * (8 + 4 * C) + nn * 4 * C + N * 8 + nn * 4 * C + N * 4 * C
+    m2p_bytes = N * 8 + nn * 4 * C + N * 4 * C
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": pr.name, "mesh_nodes": f"{n}x{n}", "particles": f"{pr.M}x{pr.M}",
+                      "channels": C, "jitter": pr.a, "shape": "quadratic", "solve": args.solve,
+                      "bins": proj.nb, "l2": "flushed between timed steps (2x L2 write)",
+                      "parallelism": "replicas only" if world > 1 else "single GPU"},
+           "roofline": {"bound": "alu", "kernel": "k_p2m (fused quadratic P2M)",
+                        "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak,
+                        "unit": "TFLOP/s",
+                        "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
+                        "traffic": None,
+                        "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
+                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+           "hbm_view": {"round_trip_bytes": rt_bytes,
+                        "round_trip_gbs": rt_bytes / (t_step * 1e-3) / 1e9,
+                        "round_trip_frac": rt_bytes / (t_step * 1e-3) / 1e9 / hbm_peak,
+                        "m2p_gbs": m2p_bytes / t_m2p / 1e9,
+                        "m2p_frac": m2p_bytes / t_m2p / 1e9 / hbm_peak,
+                        "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+           "breakdown_ms": {"build_cells": float(np.mean(cells_ms)), "p2m_quadratic": t_p2m * 1e3,
+                            "m2p": t_m2p * 1e3},
+           "gpu_launches": int(launches),
+           "clocks": clk}
+    if args.profile:
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+
+    # --- end to end through the ABI with host buffers (copies inside the timed region)
+    pos_h = torch.tensor(pr.pos, dtype=torch.float32).pin_memory()
+    vals_h = torch.tensor(pr.vals, dtype=torch.float32).pin_memory()
+    back_h = torch.empty((N, C), dtype=torch.float32).pin_memory()
+    pos_d = torch.empty_like(pos)
+    vals_d = torch.empty_like(vals)
+    def e2e_step():
+        pos_d.copy_(pos_h, non_blocking=True)
+        vals_d.copy_(vals_h, non_blocking=True)
+        proj.build(pos_d)
+        proj.p2m(vals_d, shape=P.PFEM_SHAPE_QUADRATIC, solve=solve, out=mesh)
+        proj.m2p(pos_d, mesh, out=back)
+        back_h.copy_(back, non_blocking=True)
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    ke = max(3, args.steps // 2)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / ke, world)
+    out["e2e"] = {"value": world * N / (t_e2e * 1e-3) / 1e6, "unit": UNIT,
+                  "h2d_bytes_per_step": int(pos_h.numel() * 4 + vals_h.numel() * 4),
+                  "d2h_bytes_per_step": int(back_h.numel() * 4), "ms_per_step": t_e2e}
+
+    # --- side measurements (outside the timed region)
+    def timeit(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    side = {}
+    side["p2m_linear_ms"] = timeit(lambda: proj.p2m(vals, shape=P.PFEM_SHAPE_LINEAR, out=mesh))
+    for nm, sv in (("f64", P.PFEM_SOLVE_F64), ("f32ref", P.PFEM_SOLVE_F32_REFINED), ("f32", P.PFEM_SOLVE_F32)):
+        side[f"p2m_quadratic_solve_{nm}_ms"] = timeit(
+            lambda: proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv, out=mesh))
+    # plain FP64 single-instance form: FP64 positions and fields, FP64 solve
+    pos64 = pos.double()                                     # the FP32 positions, exactly
+    vals64 = torch.tensor(pr.vals, dtype=torch.float64, device=dev)
+    proj64 = P.Projector(n, N, C=C, pos_dtype=torch.float64, device=dev)
+    mesh64 = torch.empty((n, n, C), dtype=torch.float64, device=dev)
+    back64 = torch.empty((N, C), dtype=torch.float64, device=dev)
+    def step64():
+        proj64.build(pos64)
+        proj64.p2m(vals64, shape=P.PFEM_SHAPE_QUADRATIC, out=mesh64)
+        proj64.m2p(pos64, mesh64, out=back64)
+    t64 = timeit(step64, reps=3)
+    side["fp64_round_trip_ms"] = t64
+    side["fp64_round_trip_mparticles_s"] = N / (t64 * 1e-3) / 1e6
+    proj64.check("fp64 round trip")
+    out["side"] = side
+
+    # --- accuracy on sampled nodes and particles against the FP64 oracle
+    if rank == 0 and not args.no_oracle:
+        import oracle as O
+        pos32 = pr.pos.astype(np.float32).astype(np.float64)
+        step()
+        torch.cuda.synchronize()
+        m32 = mesh.cpu().numpy()
+        b32 = back.cpu().numpy()
+        m64 = mesh64.cpu().numpy()
+        cells = O.build_cells(n, pos32)
+        rng = np.random.default_rng(0)
+        errs32, errs64, ref_max = [], [], 0.0
+        for node in rng.choice(nn, 48, replace=False):
+            J, I = divmod(int(node), n)
+            idx, w, _, _ = O.node_weights(cells, I, J, 1)
+            ref = w @ pr.vals[idx]
+            ref_max = max(ref_max, np.abs(ref).max())
+            errs32.append(np.abs(m32[J, I] - ref).max())
+            errs64.append(np.abs(m64[J, I] - ref).max())
+        vmax = np.abs(pr.vals).max()
+        sample_p = rng.choice(N, 4096, replace=False)
+        ref_b = O.m2p(n, pos32[sample_p], m32.astype(np.float64))
+        out["max_rel_err"] = {
+            "p2m_f32_vs_fp64_oracle": float(max(errs32) / vmax),
+            "p2m_f64_vs_fp64_oracle": float(max(errs64) / vmax),
+            "m2p_f32_vs_fp64_oracle": float(np.abs(b32[sample_p] - ref_b).max() / vmax),
+            "sample": "48 random nodes / 4096 random particles, error / max|field|"}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        full, work, bd = oracle_baseline(pr, 4096, 1 << 18, os.cpu_count() or 1)
+        out["cpu_baseline"] = {"value": N / full / 1e6, "unit": UNIT, "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": ("oracle bins of all particles (1 thread), quadratic P2M on "
+                                          "4096 nodes (all cores, OpenMP), M2P on 262144 particles "
+                                          "(1 thread); scaled to the full round trip"),
+                               "cpu_seconds": work, "breakdown": bd}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--solve", choices=["f32", "f32ref", "f64"], default="f32")
+    ap.add_argument("--profile", action="store_true", help="timed loop only (for ncu)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
