@@ -32,6 +32,23 @@ FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * 10) + 24
 FP32_LANES = 152 * 128
 
 
+def p2m_traffic():
+    """DRAM bytes of one k_p2m launch from the committed ncu summary, or None when the kernel
+    sources changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_p2m_traffic.txt")
+    try:
+        kv = dict(line.split()[:2] for line in open(path) if line.strip() and not line.startswith("#"))
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for f in ("p2m.cuh", "geom.cuh", "moments.cuh", "common.cuh", "p2m.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1610_05266_gb300", "csrc", f), "rb").read())
+    if kv.get("sha256") != h.hexdigest():
+        return None
+    return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -266,7 +283,8 @@ def run_ours(args, world, rank, local):
                         "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak,
                         "unit": "TFLOP/s",
                         "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
-                        "traffic": None,
+                        "traffic": p2m_traffic(),
+                        "traffic_unit": "bytes per launch (ncu dram read+write)",
                         "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
            "hbm_view": {"round_trip_bytes": rt_bytes,

@@ -114,6 +114,22 @@ pfem_status pfem_build_cells(int32_t nb, int64_t N, const void *pos, pfem_dtype 
                              int32_t *cell_start, int32_t *perm, void *pos_sorted,
                              uint32_t *q_sorted, void *ws, size_t ws_bytes, void *stream);
 
+/* The binning of pfem_build_cells (same outputs, bit for bit) without a workspace argument,
+ * for callers that cannot allocate device memory where they need the bins -- e.g. a plug-in
+ * called from a host application that owns every device allocation, or a real-time loop that
+ * must not take the device synchronisation an allocation can imply.  The paper has no
+ * counterpart.  Its scratch is a fixed array compiled into the library (36.0 MiB = 37,757,440
+ * bytes), held on every GPU that loads it until the process exits; this call allocates nothing.
+ * Limits: N <= 4,194,304 particles and nb*nb <= 1,048,576 bins, else PFEM_ERR_CAPACITY
+ * (nothing launched).  The first call on a device looks up the scratch's device address (with
+ * that device current) and caches it: make that first call before any stream capture.  All
+ * calls share the one scratch array and it keeps the last call's contents (the bin counters
+ * are cleared at the start of every call): calls that overlap on the GPU -- on different
+ * streams without ordering, or from different host threads -- race and must not be issued. */
+pfem_status pfem_build_cells_noalloc(int32_t nb, int64_t N, const void *pos, pfem_dtype pos_t,
+                                     int32_t *cell_start, int32_t *perm, void *pos_sorted,
+                                     uint32_t *q_sorted, void *stream);
+
 /* Delaunay stars (App. B: neighbours = particles joined by a Delaunay edge) of every
  * particle, counter-clockwise, in slot indices: nbrs [N, PFEM_KMAX] int32 (unused entries
  * -1), counts [N] int32.  Diagnostic entry point; the projections compute the stars they

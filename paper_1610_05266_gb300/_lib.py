@@ -36,6 +36,7 @@ SIGNATURES = {
     "pfem_read_status": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _p]),
     "pfem_reset_status": (ctypes.c_int, [_p, _p]),
     "pfem_build_cells": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p, _sz, _p]),
+    "pfem_build_cells_noalloc": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p]),
     "pfem_delaunay_stars": (ctypes.c_int, [_i32, _i64, _p, _p, _p, _p, _p, _sz, _p]),
     "pfem_shape_quadratic": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, ctypes.c_int,
                                             ctypes.c_int, _i32, _p, _p, ctypes.c_int, _p, _sz, _p]),

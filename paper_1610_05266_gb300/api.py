@@ -51,6 +51,13 @@ def pfem_build_cells(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, ws, str
           "pfem_build_cells")
 
 
+def pfem_build_cells_noalloc(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, stream=None):
+    """pfem_build_cells without a workspace (scratch compiled into the library; see pfem.h)."""
+    check(L.load().pfem_build_cells_noalloc(nb, N, ptr(pos), dtype_code(pos.dtype), ptr(cell_start),
+                                            ptr(perm), ptr(pos_sorted), ptr(q_sorted),
+                                            stream_ptr(stream)), "pfem_build_cells_noalloc")
+
+
 def pfem_delaunay_stars(nb, N, q_sorted, cell_start, nbrs, counts, ws, stream=None):
     check(L.load().pfem_delaunay_stars(nb, N, ptr(q_sorted), ptr(cell_start), ptr(nbrs),
                                        ptr(counts), ptr(ws), ws.numel() * ws.element_size(),
