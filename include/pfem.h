@@ -171,13 +171,21 @@ pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype po
                             int32_t C, const void *mesh_vals, void *vals, pfem_dtype val_t,
                             void *stream);
 
+/* Bytes of workspace pfem_project_backward needs (its own workspace; K = weights per node of
+ * the checkpointed weights, 0 in recompute mode).  Holds per-node entries [n*n, max(K,32)]
+ * and a transposed index over the N particles. */
+size_t pfem_backward_workspace_size(int32_t n, int64_t N, int32_t K);
+
 /* Adjoint of P2M with respect to particle values and positions, for an upstream gradient
  * grad_mesh [n, n, C] (each stored entry, image copies included, is its own output):
  *   grad_vals [N, C] out (original order when perm != NULL, slot order otherwise)
  *   grad_pos  [N, 2] out, same order; NULL skips the position gradient
  * Topology is held fixed.  mode RECOMPUTE rebuilds the shape functions; mode CHECKPOINT
  * reads w_idx/w from pfem_shape_quadratic for the value gradient (positions are always
- * recomputed).  Deterministic: no atomics.  Values must be FP32 or FP64. */
+ * recomputed).  Deterministic: per-node entries, then a per-particle gather through a stable
+ * counting sort (no atomics on values).  Values FP32 (solve F32 or F64) or FP64 (solve F64);
+ * ws is a separate workspace of pfem_backward_workspace_size() bytes whose status word records
+ * device errors.  A node with more than 32 distinct particles records PFEM_ERR_CAPACITY. */
 pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                   pfem_dtype pos_t, const uint32_t *q_sorted,
                                   const int32_t *cell_start, const int32_t *perm, int32_t C,

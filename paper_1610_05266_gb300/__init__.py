@@ -7,3 +7,4 @@ The CUDA library is required: importing the binding never falls back to a CPU pa
 from ._lib import LibraryMissing, PfemError, load  # noqa: F401
 from .api import *  # noqa: F401,F403
 from .api import Projector, Cells  # noqa: F401
+from . import autograd  # noqa: F401

@@ -89,6 +89,10 @@ def pfem_interp_m2p(n, N, pos, C, mesh_vals, vals, stream=None):
           "pfem_interp_m2p")
 
 
+def pfem_backward_workspace_size(n: int, N: int, K: int) -> int:
+    return int(L.load().pfem_backward_workspace_size(n, N, K))
+
+
 def pfem_project_backward(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape,
                           solve, mode, w_idx, w, K, grad_mesh, grad_vals, grad_pos, ws,
                           stream=None):
@@ -193,6 +197,44 @@ class Projector:
             out = torch.empty((pos.shape[0], C), dtype=mesh.dtype, device=mesh.device)
         pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream)
         return out
+
+    def backward(self, vals: torch.Tensor, grad_mesh: torch.Tensor, shape=PFEM_SHAPE_QUADRATIC,
+                 solve=None, weights=None, want_pos: bool = True, sorted_vals: bool = False,
+                 stream=None):
+        """Adjoint of p2m: (grad_vals [N,C], grad_pos [N,2] or None), same order as vals.
+        With `weights` (from shape_weights) the value gradient uses them (checkpoint mode)."""
+        c = self.cells
+        C = vals.shape[1]
+        if solve is None:
+            solve = PFEM_SOLVE_F64 if vals.dtype == torch.float64 else PFEM_SOLVE_F32
+        w_idx, w = weights if weights is not None else (None, None)
+        K = w_idx.shape[1] if w_idx is not None else 0
+        mode = PFEM_BACKWARD_CHECKPOINT if weights is not None else PFEM_BACKWARD_RECOMPUTE
+        nbytes = pfem_backward_workspace_size(self.n, self.N, K)
+        if getattr(self, "_bws", None) is None or self._bws.numel() * 8 < nbytes:
+            self._bws = torch.zeros((nbytes + 7) // 8, dtype=torch.float64, device=self.device)
+        else:
+            pfem_reset_status(self._bws, stream)
+        gv = torch.empty_like(vals)
+        gp = torch.empty((self.N, 2), dtype=vals.dtype, device=self.device) if want_pos else None
+        pfem_project_backward(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
+                              None if sorted_vals else c.perm, C, vals, shape, solve, mode, w_idx,
+                              w, K, grad_mesh.contiguous(), gv, gp, self._bws, stream)
+        return gv, gp
+
+    def backward_status(self, stream=None) -> Tuple[int, int]:
+        return pfem_read_status(self._bws, stream)
+
+    def m2p_backward(self, pos: torch.Tensor, mesh: torch.Tensor, grad_vals: torch.Tensor,
+                     want_pos: bool = True, stream=None):
+        """Adjoint of m2p for positions binned by the last build(pos)."""
+        c = self.cells
+        C = mesh.shape[-1]
+        gm = torch.empty_like(mesh)
+        gp = torch.empty((pos.shape[0], 2), dtype=mesh.dtype, device=self.device) if want_pos else None
+        pfem_interp_m2p_backward(self.n, self.nb, pos.shape[0], pos, c.cell_start, c.perm, C,
+                                 mesh.contiguous(), grad_vals.contiguous(), gm, gp, stream)
+        return gm, gp
 
     def status(self, stream=None) -> Tuple[int, int]:
         return pfem_read_status(self.cells.ws, stream)

@@ -1,0 +1,445 @@
+// backward.cu -- adjoint of P2M with respect to particle values and positions (no paper
+// counterpart; the paper only runs the forward projection).
+//
+// Forward, per node i:  alpha_i = sum_mu w_{i mu}(r) alpha_mu  with
+//   w_{i mu} = lambda_mu [mu in T] + sum_{e=(nu,sg) in T} c_e A_{mu e},   c_e = 2 lambda_nu lambda_sg,
+//   A_{mu e} = p_mu . y_e,  M_e y_e = b_e,  M_e = sum_{mu in S_e} p_mu p_mu^T.
+// With beta_mu = gbar_i . alpha_mu, the node contributes
+//   dL/dalpha_mu += w_{i mu} gbar_i,
+//   dL/dr via lambda (barycentric cofactors) and via every edge: u = sum beta_mu p_mu,
+//   B_e = u . y_e, z = M_e^{-1} u (one extra solve), and for each stencil member
+//   pbar_mu = c_e [(beta_mu - z.p_mu) y_e - (y_e.p_mu) z],  tbar from b_e, lambdabar from c_e B_e.
+// The frame (edge midpoint, edge length) is held fixed: A does not depend on it (eq. A2_2), so
+// the derivative at a fixed frame is the derivative of A.
+//
+// Determinism without atomics on values: phase 1 writes each node's entries (slot, w, dpos)
+// into [n*n, K] arrays; phase 2 builds a transposed index by a stable counting sort keyed by
+// particle slot (entries per particle ordered by entry id) and gathers per particle.
+#include "internal.h"
+#include "p2m.cuh"
+
+namespace pfem {
+
+struct BwdArgs {
+    P2MArgs f;                  // forward geometry/values (f.out unused)
+    const void *grad_mesh;      // [n*n, C]
+    int K;                      // entries per node
+    int *e_slot;                // [n*n*K]
+    void *e_w;                  // [n*n*K] R
+    void *e_dpos;               // [n*n*K*2] R (may be null: value gradient only)
+};
+
+constexpr int KBWD = 32;   // distinct particles per node kept by the recompute kernel
+
+template <typename R> struct Entry {
+    int slot;
+    R w, dx, dy;
+};
+
+template <typename R>
+__device__ __forceinline__ int entry_of(Entry<R> *E, int &cnt, int K, int s, bool &over)
+{
+    for (int i = 0; i < cnt; ++i)
+        if (E[i].slot == s) return i;
+    if (cnt == K) { over = true; return -1; }
+    E[cnt].slot = s;
+    E[cnt].w = E[cnt].dx = E[cnt].dy = R(0);
+    return cnt++;
+}
+
+template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
+__device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
+{
+    const P2MArgs &a = b.f;
+    const int nc = a.n - 1;
+    const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+    const long long node = (long long)J * a.n + I;
+    int *oslot = b.e_slot + node * b.K;
+    R *ow = (R *)b.e_w + node * b.K;
+    R *od = POS ? (R *)b.e_dpos + node * b.K * 2 : nullptr;
+
+    R g[8];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        g[c] = c < a.C ? load_val<V, R>((const V *)b.grad_mesh + node * a.C + c) : R(0);
+        any |= g[c] != R(0);
+    }
+    Entry<R> E[KBWD];
+    int cnt = 0;
+    bool over = false;
+    int st = 0;
+    if (any) {
+        const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+        int tri[3];
+        int stars[3][KMAX];
+        int ns[3] = {0, 0, 0};
+        st = locate(a.B, qn, a.R0, tri, stars[0], ns[0]);
+        if (SHAPE == PFEM_SHAPE_QUADRATIC && st == 0)
+            for (int e = 0; e < 3 && st == 0; ++e)
+                if (ns[e] == 0) {
+                    const int c = star_of(a.B, tri[e], a.R0, stars[e]);
+                    if (c < 0) st = c;
+                    else ns[e] = c;
+                }
+        if (st == 0) {
+            NodePos<P, R> np;
+            np.init(Iu, Ju, nc);
+            R d[3][2];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
+            const R Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
+            const R Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
+            const R Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
+            const R A2 = Na + Nb + Nc;
+            const R lam[3] = {Na / A2, Nb / A2, Nc / A2};
+            R lbar[3] = {R(0), R(0), R(0)};
+            auto beta_of = [&](int s) {
+                R v[8];
+                load_vals<V, R>((const V *)a.vals, a.perm, s, a.C, v);
+                R t = R(0);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < a.C) t = fma(g[c], v[c], t);
+                return t;
+            };
+            int ti[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                ti[e] = entry_of(E, cnt, b.K, tri[e], over);
+                if (ti[e] >= 0) E[ti[e]].w += lam[e];
+                lbar[e] += beta_of(tri[e]);
+            }
+            if (SHAPE == PFEM_SHAPE_QUADRATIC) {
+                for (int e = 0; e < 3 && st == 0 && !over; ++e) {
+                    const int f = e == 2 ? 0 : e + 1;
+                    const int nu = tri[e], sg = tri[f];
+                    const int *st_nu = stars[e], *st_sg = stars[f];
+                    const int n_nu = ns[e], n_sg = ns[f];
+                    const S rnx = S(d[e][0]), rny = S(d[e][1]), rsx = S(d[f][0]), rsy = S(d[f][1]);
+                    const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
+                    const S ex = rnx - rsx, ey = rny - rsy;
+                    const S inv = S(1) / sqrt(ex * ex + ey * ey);
+                    auto for_stencil = [&](auto &&fn) {
+                        fn(nu);
+                        for (int i = 0; i < n_nu; ++i) fn(st_nu[i]);
+                        for (int j = 0; j < n_sg; ++j) {
+                            const int m = st_sg[j];
+                            if (m == nu || in_list(st_nu, n_nu, m)) continue;
+                            fn(m);
+                        }
+                    };
+                    auto coords = [&](int s, S &x, S &y) {
+                        R dx, dy;
+                        np.off(a.pos, s, dx, dy);
+                        x = (S(dx) - mx) * inv;
+                        y = (S(dy) - my) * inv;
+                    };
+                    Moment<S> M;
+                    M.zero();
+                    S u[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+                    for_stencil([&](int s) {
+                        S x, y;
+                        coords(s, x, y);
+                        M.add(x, y);
+                        const S bt = S(beta_of(s));
+                        const S p[6] = {S(1), x, y, x * x, x * y, y * y};
+#pragma unroll
+                        for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
+                    });
+                    if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
+                    const S tx = ex * inv, ty = ey * inv;
+                    const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
+                                     S(-0.5) * ty * ty};
+                    S y[6], z[6];
+                    M.solve(bb, y);
+                    M.solve(u, z);
+                    const S ce = S(2) * S(lam[e]) * S(lam[f]);
+                    S Be = S(0);
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) Be = fma(u[r], y[r], Be);
+                    lbar[e] += R(S(2) * S(lam[f]) * Be);
+                    lbar[f] += R(S(2) * S(lam[e]) * Be);
+                    for_stencil([&](int s) {
+                        S x, yy;
+                        coords(s, x, yy);
+                        const S p[6] = {S(1), x, yy, x * x, x * yy, yy * yy};
+                        S Am = S(0), Zm = S(0);
+#pragma unroll
+                        for (int r = 0; r < 6; ++r) {
+                            Am = fma(p[r], y[r], Am);
+                            Zm = fma(p[r], z[r], Zm);
+                        }
+                        const int k = entry_of(E, cnt, b.K, s, over);
+                        if (k < 0) return;
+                        E[k].w += R(ce * Am);
+                        if (POS) {
+                            const S bt = S(beta_of(s));
+                            S pb[6];
+#pragma unroll
+                            for (int r = 0; r < 6; ++r) pb[r] = ce * ((bt - Zm) * y[r] - Am * z[r]);
+                            const S xb = pb[1] + S(2) * x * pb[3] + yy * pb[4];
+                            const S yb = pb[2] + x * pb[4] + S(2) * yy * pb[5];
+                            E[k].dx += R(xb * inv);
+                            E[k].dy += R(yb * inv);
+                        }
+                    });
+                    if (POS && !over) {
+                        // b = [0,0,0,-tx^2/2,-tx ty/2,-ty^2/2], t = (r_nu - r_sg)/s
+                        const S txb = ce * (-tx * z[3] - S(0.5) * ty * z[4]);
+                        const S tyb = ce * (-S(0.5) * tx * z[4] - ty * z[5]);
+                        E[ti[e]].dx += R(txb * inv);
+                        E[ti[e]].dy += R(tyb * inv);
+                        E[ti[f]].dx -= R(txb * inv);
+                        E[ti[f]].dy -= R(tyb * inv);
+                    }
+                }
+            }
+            if (POS && st == 0 && !over) {
+                // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
+                const R Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
+                const R nb0 = (lbar[0] - Lam) / A2, nb1 = (lbar[1] - Lam) / A2, nb2 = (lbar[2] - Lam) / A2;
+                // cross(u, v): d/du = (v.y, -v.x), d/dv = (-u.y, u.x)
+                R gx[3] = {R(0), R(0), R(0)}, gy[3] = {R(0), R(0), R(0)};
+                gx[1] += nb0 * d[2][1];  gy[1] -= nb0 * d[2][0];
+                gx[2] -= nb0 * d[1][1];  gy[2] += nb0 * d[1][0];
+                gx[2] += nb1 * d[0][1];  gy[2] -= nb1 * d[0][0];
+                gx[0] -= nb1 * d[2][1];  gy[0] += nb1 * d[2][0];
+                gx[0] += nb2 * d[1][1];  gy[0] -= nb2 * d[1][0];
+                gx[1] -= nb2 * d[0][1];  gy[1] += nb2 * d[0][0];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    E[ti[e]].dx += gx[e];
+                    E[ti[e]].dy += gy[e];
+                }
+            }
+        }
+        if (over && st == 0) st = -PFEM_ERR_CAPACITY;
+        if (st != 0) {
+            record_error(a.status, -st, node);
+            cnt = 0;
+        }
+    }
+    for (int k = 0; k < b.K; ++k) {
+        const bool v = k < cnt;
+        oslot[k] = v ? E[k].slot : -1;
+        ow[k] = v ? E[k].w : R(0);
+        if (POS) {
+            od[2 * k] = v ? E[k].dx : R(0);
+            od[2 * k + 1] = v ? E[k].dy : R(0);
+        }
+    }
+}
+
+template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
+__global__ void __launch_bounds__(128) k_bwd_node(BwdArgs b)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= b.f.n || J >= b.f.n) return;
+    bwd_node<P, V, R, S, SHAPE, POS>(b, I, J);
+}
+
+// ---------------------------------------------------------------- transposed gather
+
+__global__ void k_tr_count(long long E, const int *__restrict__ slot, int *__restrict__ count,
+                           int *__restrict__ rank)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = slot[e];
+        rank[e] = s >= 0 ? atomicAdd(count + s, 1) : -1;
+    }
+}
+
+__global__ void k_tr_scatter(long long E, const int *__restrict__ slot, const int *__restrict__ rank,
+                             const int *__restrict__ start, int *__restrict__ order)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = slot[e];
+        if (s >= 0) order[__ldg(start + s) + rank[e]] = (int)e;
+    }
+}
+
+__global__ void k_tr_sort(long long N, const int *__restrict__ start, int *order)
+{
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int a = start[s], b = start[s + 1];
+        for (int i = a + 1; i < b; ++i) {
+            const int v = order[i];
+            int j = i - 1;
+            while (j >= a && order[j] > v) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = v;
+        }
+    }
+}
+
+// grad_vals[particle] = sum_e w_e gbar_node(e); grad_pos[particle] = sum_e dpos_e
+template <typename V, typename R, typename W>
+__global__ void k_tr_gather(long long N, int K, int C, const int *__restrict__ start,
+                            const int *__restrict__ order, const W *__restrict__ ew,
+                            const R *__restrict__ edpos, const V *__restrict__ grad_mesh,
+                            const int *__restrict__ perm, V *__restrict__ grad_vals,
+                            V *__restrict__ grad_pos)
+{
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        R gv[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) gv[c] = R(0);
+        R gx = R(0), gy = R(0);
+        const int a = __ldg(start + s), b = __ldg(start + s + 1);
+        for (int i = a; i < b; ++i) {
+            const int e = __ldg(order + i);
+            const long long node = e / K;
+            const R w = (R)__ldg(ew + e);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < C) gv[c] = fma(w, load_val<V, R>(grad_mesh + node * C + c), gv[c]);
+            if (edpos) {
+                gx += __ldg(edpos + 2LL * e);
+                gy += __ldg(edpos + 2LL * e + 1);
+            }
+        }
+        const long long o = perm ? (long long)__ldg(perm + s) : s;
+        if (grad_vals)
+            for (int c = 0; c < C; ++c) store_val<V, R>(grad_vals + o * C + c, gv[c]);
+        if (grad_pos && edpos) {
+            store_val<V, R>(grad_pos + 2 * o, gx);
+            store_val<V, R>(grad_pos + 2 * o + 1, gy);
+        }
+    }
+}
+
+static unsigned grid1(long long work, int threads)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152LL * 64) b = 152LL * 64;
+    return (unsigned)b;
+}
+
+BwdLayout bwd_layout(int n, long long N, int Kw)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    BwdLayout L;
+    L.K = KBWD;
+    const int K = Kw > KBWD ? Kw : KBWD;
+    const long long E = (long long)n * n * K;
+    size_t off = 256;
+    L.e_slot = off;  off = al(off + 4 * (size_t)E);
+    L.e_w = off;     off = al(off + 8 * (size_t)E);
+    L.e_dpos = off;  off = al(off + 16 * (size_t)E);
+    L.count = off;   off = al(off + 4 * (size_t)(N + 1));
+    L.start = off;   off = al(off + 4 * (size_t)(N + 1));
+    L.rank = off;    off = al(off + 4 * (size_t)E);
+    L.order = off;   off = al(off + 4 * (size_t)E);
+    L.scan = off;    off = al(off + 4 * scan_scratch_ints(N + 1));
+    L.total = off;
+    return L;
+}
+
+// Phase 2 over entries (slot, w, dpos) laid out [n*n, K].
+template <typename V, typename R, typename W>
+static cudaError_t transposed_gather(int n, long long N, int K, int C, const int *e_slot,
+                                     const W *e_w, const R *e_dpos, const void *grad_mesh,
+                                     const int *perm, void *grad_vals, void *grad_pos,
+                                     const BwdLayout &L, char *ws, cudaStream_t s)
+{
+    const long long E = (long long)n * n * K;
+    int *count = (int *)(ws + L.count);
+    int *start = (int *)(ws + L.start);
+    int *rank = (int *)(ws + L.rank);
+    int *order = (int *)(ws + L.order);
+    cudaError_t e = cudaMemsetAsync(count, 0, 4 * (size_t)(N + 1), s);
+    if (e != cudaSuccess) return e;
+    k_tr_count<<<grid1(E, 256), 256, 0, s>>>(E, e_slot, count, rank);
+    count_launch();
+    e = scan_exclusive(count, start, N + 1, (int *)(ws + L.scan), s);
+    if (e != cudaSuccess) return e;
+    k_tr_scatter<<<grid1(E, 256), 256, 0, s>>>(E, e_slot, rank, start, order);
+    k_tr_sort<<<grid1(N, 128), 128, 0, s>>>(N, start, order);
+    k_tr_gather<V, R, W><<<grid1(N, 128), 128, 0, s>>>(N, K, C, start, order, e_w, e_dpos,
+                                                       (const V *)grad_mesh, perm, (V *)grad_vals,
+                                                       (V *)grad_pos);
+    count_launch(3);
+    return cudaGetLastError();
+}
+
+template <typename P, typename V, typename R, typename S, int SHAPE>
+static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *vals,
+                         const void *grad_mesh, void *grad_vals, void *grad_pos, bool checkpoint,
+                         const int *w_idx, const void *w, int Kw, const BwdLayout &L, char *ws,
+                         cudaStream_t s)
+{
+    const int K = L.K;
+    BwdArgs b;
+    b.f.n = g.n;
+    b.f.B.q = (const uint2 *)g.q_sorted;
+    b.f.B.start = g.cell_start;
+    b.f.B.nb = g.nb;
+    b.f.B.rmax = g.rmax;
+    b.f.R0 = g.R0;
+    b.f.pos = g.pos_sorted;
+    b.f.perm = perm;
+    b.f.vals = vals;
+    b.f.C = C;
+    b.f.out = nullptr;
+    b.f.w_idx = nullptr;
+    b.f.w = nullptr;
+    b.f.K = 0;
+    b.f.status = (DevStatus *)ws;
+    b.grad_mesh = grad_mesh;
+    b.K = K;
+    b.e_slot = (int *)(ws + L.e_slot);
+    b.e_w = ws + L.e_w;
+    b.e_dpos = ws + L.e_dpos;
+    const dim3 grid((g.n + 15) / 16, (g.n + 7) / 8);
+    if (checkpoint) {
+        // value gradient straight from the stored weights
+        cudaError_t e = transposed_gather<V, R, R>(g.n, g.N, Kw, C, w_idx, (const R *)w,
+                                                   (const R *)nullptr, grad_mesh, perm, grad_vals,
+                                                   nullptr, L, ws, s);
+        if (e != cudaSuccess || !grad_pos) return e;
+        k_bwd_node<P, V, R, S, SHAPE, true><<<grid, 128, 0, s>>>(b);
+        count_launch();
+        return transposed_gather<V, R, R>(g.n, g.N, K, C, b.e_slot, (const R *)b.e_w,
+                                          (const R *)b.e_dpos, grad_mesh, perm, nullptr, grad_pos,
+                                          L, ws, s);
+    }
+    if (grad_pos) {
+        k_bwd_node<P, V, R, S, SHAPE, true><<<grid, 128, 0, s>>>(b);
+    } else {
+        b.e_dpos = nullptr;
+        k_bwd_node<P, V, R, S, SHAPE, false><<<grid, 128, 0, s>>>(b);
+    }
+    count_launch();
+    return transposed_gather<V, R, R>(g.n, g.N, K, C, b.e_slot, (const R *)b.e_w,
+                                      grad_pos ? (const R *)b.e_dpos : nullptr, grad_mesh, perm,
+                                      grad_vals, grad_pos, L, ws, s);
+}
+
+cudaError_t launch_p2m_backward(const GeoArgs &g, const int *perm, int C, const void *vals,
+                                pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
+                                bool checkpoint, const int *w_idx, const void *w, int Kw,
+                                const void *grad_mesh, void *grad_vals, void *grad_pos,
+                                const BwdLayout &L, void *ws, cudaStream_t s)
+{
+    char *W = (char *)ws;
+    const bool q = shape == PFEM_SHAPE_QUADRATIC;
+    if (val_t == PFEM_F64) {
+        if (q) return bwd_t<double, double, double, double, 1>(g, perm, C, vals, grad_mesh, grad_vals, grad_pos, checkpoint, w_idx, w, Kw, L, W, s);
+        return bwd_t<double, double, double, double, 0>(g, perm, C, vals, grad_mesh, grad_vals, grad_pos, checkpoint, w_idx, w, Kw, L, W, s);
+    }
+    if (!q) return bwd_t<float, float, float, float, 0>(g, perm, C, vals, grad_mesh, grad_vals, grad_pos, checkpoint, w_idx, w, Kw, L, W, s);
+    if (solve == PFEM_SOLVE_F64)
+        return bwd_t<float, float, float, double, 1>(g, perm, C, vals, grad_mesh, grad_vals, grad_pos, checkpoint, w_idx, w, Kw, L, W, s);
+    return bwd_t<float, float, float, float, 1>(g, perm, C, vals, grad_mesh, grad_vals, grad_pos, checkpoint, w_idx, w, Kw, L, W, s);
+}
+
+}  // namespace pfem

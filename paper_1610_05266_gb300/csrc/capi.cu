@@ -216,6 +216,12 @@ pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype po
     return from_cuda(launch_m2p(n, N, pos, pos_t, C, mesh_vals, vals, val_t, (cudaStream_t)stream));
 }
 
+size_t pfem_backward_workspace_size(int32_t n, int64_t N, int32_t K)
+{
+    if (n < 1 || N < 0 || K < 0) return 0;
+    return bwd_layout(n, N, K).total;
+}
+
 pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                   pfem_dtype pos_t, const uint32_t *q_sorted,
                                   const int32_t *cell_start, const int32_t *perm, int32_t C,
@@ -225,11 +231,29 @@ pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *
                                   pfem_dtype w_t, const void *grad_mesh, void *grad_vals,
                                   void *grad_pos, void *ws, size_t ws_bytes, void *stream)
 {
-    (void)n; (void)nb; (void)N; (void)pos_sorted; (void)pos_t; (void)q_sorted; (void)cell_start;
-    (void)perm; (void)C; (void)vals; (void)val_t; (void)shape; (void)solve; (void)mode;
-    (void)w_idx; (void)w; (void)K; (void)w_t; (void)grad_mesh; (void)grad_vals; (void)grad_pos;
-    (void)ws; (void)ws_bytes; (void)stream;
-    return PFEM_ERR_INVALID_ARG;
+    GeoArgs g;
+    if (!make_geo(n, nb, N, pos_sorted, pos_t, q_sorted, cell_start, &g)) return PFEM_ERR_INVALID_ARG;
+    if (C < 1 || C > 8 || !vals || !grad_mesh || !grad_vals || !ws) return PFEM_ERR_INVALID_ARG;
+    if (shape != PFEM_SHAPE_LINEAR && shape != PFEM_SHAPE_QUADRATIC) return PFEM_ERR_INVALID_ARG;
+    if (val_t == PFEM_F64) {
+        if (pos_t != PFEM_F64 || solve != PFEM_SOLVE_F64) return PFEM_ERR_INVALID_ARG;
+    } else if (val_t == PFEM_F32) {
+        if (pos_t != PFEM_F32 || (solve != PFEM_SOLVE_F64 && solve != PFEM_SOLVE_F32))
+            return PFEM_ERR_INVALID_ARG;
+    } else {
+        return PFEM_ERR_INVALID_ARG;
+    }
+    const bool ckpt = mode == PFEM_BACKWARD_CHECKPOINT;
+    if (mode != PFEM_BACKWARD_RECOMPUTE && !ckpt) return PFEM_ERR_INVALID_ARG;
+    if (ckpt) {
+        if (!w_idx || !w || K < 3 || K > PFEM_KW_MAX) return PFEM_ERR_INVALID_ARG;
+        if (w_t != val_t) return PFEM_ERR_INVALID_ARG;
+    }
+    const BwdLayout L = bwd_layout(n, N, ckpt ? K : 0);
+    if (ws_bytes < L.total) return PFEM_ERR_WORKSPACE;
+    return from_cuda(launch_p2m_backward(g, perm, C, vals, val_t, shape, solve, ckpt, w_idx, w,
+                                         ckpt ? K : 0, grad_mesh, grad_vals, grad_pos, L, ws,
+                                         (cudaStream_t)stream));
 }
 
 pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const void *pos,
@@ -238,9 +262,17 @@ pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const voi
                                      const void *grad_vals, pfem_dtype val_t, void *grad_mesh,
                                      void *grad_pos, void *stream)
 {
-    (void)n; (void)nb; (void)N; (void)pos; (void)pos_t; (void)cell_start; (void)perm; (void)C;
-    (void)mesh_vals; (void)grad_vals; (void)val_t; (void)grad_mesh; (void)grad_pos; (void)stream;
-    return PFEM_ERR_INVALID_ARG;
+    if (n < 9 || nb < 1 || (long long)nb * nb >= (1LL << 30) || N < 0 || N >= (1LL << 31) ||
+        C < 1 || C > 8)
+        return PFEM_ERR_INVALID_ARG;
+    if (!cell_start || !grad_mesh || (N > 0 && (!pos || !perm || !grad_vals)) ||
+        (grad_pos && !mesh_vals))
+        return PFEM_ERR_INVALID_ARG;
+    if (pos_t != PFEM_F64 && pos_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
+    if (val_t != PFEM_F64 && val_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
+    return from_cuda(launch_m2p_backward(n, nb, N, pos, pos_t, cell_start, perm, C, mesh_vals,
+                                         grad_vals, val_t, grad_mesh, grad_pos,
+                                         (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -142,7 +142,7 @@ __device__ __forceinline__ int circ_filter(const Circ &c, int2 p)
 // Exact incircle with the tie-break.  Points are relative to v (the origin); qv, qa, qb, qc
 // are the absolute fixed-point coordinates that give the keys.  Returns +1 when c is inside
 // circle(v, a, b) (perturbed), -1 otherwise.
-__device__ __noinline__ int incircle_exact(int2 a, int2 b, int2 c, uint2 qv, uint2 qa,
+static __device__ __noinline__ int incircle_exact(int2 a, int2 b, int2 c, uint2 qv, uint2 qa,
                                            uint2 qb, uint2 qc)
 {
     const long long la = (long long)a.x * a.x + (long long)a.y * a.y;
@@ -212,7 +212,7 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
 
 // Counter-clockwise Delaunay star of slot v into nbrs[0..count).  Returns count >= 3, or
 // -PFEM_ERR_* on failure.
-__device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
+static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
 {
     const uint2 pv = __ldg(B.q + v);
     for (int R = R0; R <= B.rmax; ++R) {
@@ -261,7 +261,7 @@ __device__ __forceinline__ int apex_of(const Bins &B, int u, int w, int R0)
 // Locate fixed-point point p in the Delaunay triangulation: tri = counter-clockwise triangle
 // containing p (boundary included).  On success also returns the star of tri[0] in star0
 // (count n0) when tri[0] is the particle nearest to p, else n0 = 0.  Returns 0 or -PFEM_ERR_*.
-__device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tri[3], int *star0, int &n0)
+static __device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tri[3], int *star0, int &n0)
 {
     n0 = 0;
     int v0 = -1;

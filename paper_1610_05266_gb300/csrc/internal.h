@@ -48,4 +48,20 @@ cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st
 cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, int C,
                        const void *mesh, void *vals, pfem_dtype val_t, cudaStream_t s);
 
+struct BwdLayout {
+    int K;   // entries per node written by the recompute kernel
+    size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, total;
+};
+BwdLayout bwd_layout(int n, long long N, int K);
+
+cudaError_t launch_p2m_backward(const GeoArgs &g, const int *perm, int C, const void *vals,
+                                pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
+                                bool checkpoint, const int *w_idx, const void *w, int Kw,
+                                const void *grad_mesh, void *grad_vals, void *grad_pos,
+                                const BwdLayout &L, void *ws, cudaStream_t s);
+cudaError_t launch_m2p_backward(int n, int nb, long long N, const void *pos, pfem_dtype pos_t,
+                                const int *cell_start, const int *perm, int C, const void *mesh,
+                                const void *gv, pfem_dtype val_t, void *gm, void *gp,
+                                cudaStream_t s);
+
 }  // namespace pfem
