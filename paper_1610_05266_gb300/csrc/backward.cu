@@ -384,6 +384,7 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
     b.f.B.start = g.cell_start;
     b.f.B.nb = g.nb;
     b.f.B.rmax = g.rmax;
+    b.f.B.dmax = g.dmax;
     b.f.R0 = g.R0;
     b.f.pos = g.pos_sorted;
     b.f.perm = perm;

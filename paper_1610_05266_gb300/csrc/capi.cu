@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" entry points declared in include/pfem.h: argument checks,
 // workspace layout and dispatch to the kernels.  No entry point allocates device memory.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -75,6 +76,11 @@ static bool make_geo(int32_t n, int32_t nb, int64_t N, const void *pos_sorted, p
     g->q_sorted = q_sorted;
     g->cell_start = cell_start;
     radii(nb, N, &g->R0, &g->rmax);
+    // distance cutoff of the first star attempt: 2.5 mean particle spacings (fixed point)
+    g->dmax = (float)std::fmin(2.5 * 4294967296.0 / std::sqrt((double)N), 1073741824.0);
+    // The shared-memory tiled P2M is opt-in: on the jittered-lattice workloads it measured
+    // slower than the per-thread kernel (the cost is in the divergent star search, not memory).
+    g->tiled = getenv("PFEM_TILED") != nullptr;
     return g->rmax >= g->R0;
 }
 

@@ -24,6 +24,7 @@ struct Bins {
     const int *__restrict__ start;    // [nb*nb + 1]
     int nb;
     int rmax;                         // largest search radius (bins) tried before giving up
+    float dmax;                       // candidate distance cutoff of the first attempt (fixed point)
 };
 
 __device__ __forceinline__ int2 rel(uint2 a, uint2 o)
@@ -174,9 +175,14 @@ static __device__ __noinline__ int incircle_exact(int2 a, int2 b, int2 c, uint2 
 // Apex of the Delaunay triangle to the left of the directed edge v -> w, among the region's
 // particles.  Returns its slot, or -1 when there is none or its circumcircle is not certified
 // to lie inside the region.
-__device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, const Region &g)
+// With a cutoff D (dmax > 0), candidates farther than D from v are skipped, and the result is
+// certified only if the circumcircle also lies within distance D of v (its diameter through v
+// is at most D), so that no skipped particle can be inside it.
+__device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, const Region &g,
+                                           float dmax = 0.f)
 {
     const int2 dw = rel(pw, pv);
+    const float d2cut = dmax > 0.f ? dmax * dmax : 3.4e38f;
     int best = -1;
     int2 db = make_int2(0, 0);
     uint2 qb = make_uint2(0, 0);
@@ -185,6 +191,8 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
     for_region(B, g, [&](int s) {
         const uint2 qs = __ldg(B.q + s);
         const int2 dc = rel(qs, pv);
+        const float fx = (float)dc.x, fy = (float)dc.y;
+        if (fmaf(fx, fx, fy * fy) > d2cut) return;    // beyond the cutoff
         if (cross(dw, dc) <= 0) return;               // not strictly left of v -> w
         if (best >= 0) {
             int t = circ_filter(cb, dc);
@@ -207,7 +215,122 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
     if (cx - ext < -g.cl_lo_x || cx + ext > g.cl_hi_x || cy - ext < -g.cl_lo_y ||
         cy + ext > g.cl_hi_y)
         return -1;
+    if (dmax > 0.f && 2.f * ext > dmax * 0.9999f) return -1;
     return best;
+}
+
+// ---------------------------------------------------------------- list-based star (fast path)
+// The candidates within distance D of v are gathered once into a per-thread list of FP32
+// coordinates relative to v (exact when |d| < 2^24), and the gift-wrap scans run over the
+// list with FP32-filtered orientation and incircle tests; a test the filter cannot decide is
+// redone exactly from the fixed-point coordinates.  Every returned triangle is certified: its
+// circumcircle lies inside the searched region and within distance D of v, so no particle
+// left out of the list can be inside it.
+
+constexpr int KL = 24;   // list capacity
+
+struct FCirc {
+    float K, P, Q, Ka, Pa, Qa;
+};
+
+__device__ __forceinline__ FCirc make_fcirc(float ax, float ay, float bx, float by)
+{
+    FCirc c;
+    const float la = fmaf(ax, ax, ay * ay), lb = fmaf(bx, bx, by * by);
+    const float k1 = ax * by, k2 = ay * bx;
+    const float t1 = lb * ay, t2 = la * by, t3 = la * bx, t4 = lb * ax;
+    c.K = k1 - k2;  c.Ka = fabsf(k1) + fabsf(k2);
+    c.P = t1 - t2;  c.Pa = fabsf(t1) + fabsf(t2);
+    c.Q = t3 - t4;  c.Qa = fabsf(t3) + fabsf(t4);
+    return c;
+}
+
+// +1 inside, -1 outside, 0 undecided.  Inputs carry at most one rounding each; the bound
+// (2^-19 of the summed magnitudes, 32 roundings) covers inputs, K/P/Q and the evaluation.
+__device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
+{
+    const float l = fmaf(x, x, y * y);
+    const float det = fmaf(c.K, l, fmaf(c.P, x, c.Q * y));
+    const float mag = fmaf(c.Ka, l, fmaf(c.Pa, fabsf(x), c.Qa * fabsf(y)));
+    const float bound = 1.9073486328125e-06f * mag;
+    return det < -bound ? 1 : (det > bound ? -1 : 0);
+}
+
+static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
+                                             float D, int *nbrs)
+{
+    float lx[KL], ly[KL];
+    int lid[KL];
+    int cnt = 0, u0 = -1, s0 = 0x7fffffff;
+    long long d2b = 0x7fffffffffffffffLL;
+    bool dup = false, over = false;
+    const float D2 = D * D;
+    for_region(B, g, [&](int s) {
+        if (s == v) return;
+        const int2 d = rel(__ldg(B.q + s), pv);
+        const float fx = (float)d.x, fy = (float)d.y;
+        if (fmaf(fx, fx, fy * fy) > D2) return;
+        const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
+        dup |= d2 == 0;
+        if (cnt == KL) { over = true; return; }
+        lx[cnt] = fx; ly[cnt] = fy; lid[cnt] = s;
+        if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; }
+        ++cnt;
+    });
+    if (dup) return -PFEM_ERR_DEGENERATE;
+    if (over || u0 < 0) return -1;
+    const float clx = g.cl_lo_x, chx = g.cl_hi_x, cly = g.cl_lo_y, chy = g.cl_hi_y;
+    int cur = u0, n = 0;
+    for (;;) {
+        if (n == KMAX) return -PFEM_ERR_CAPACITY;
+        nbrs[n++] = lid[cur];
+        const float wx = lx[cur], wy = ly[cur];
+        int best = -1;
+        FCirc cb;
+        cb.K = cb.P = cb.Q = cb.Ka = cb.Pa = cb.Qa = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+            if (k == cur) continue;
+            const float cx = lx[k], cy = ly[k];
+            // orientation of (v, w, c): FP32 filter, exact on ties
+            const float o1 = wx * cy, o2 = wy * cx;
+            const float o = o1 - o2;
+            const float ob = 4.76837158203125e-07f * (fabsf(o1) + fabsf(o2));
+            int left;
+            if (o > ob) left = 1;
+            else if (o < -ob) left = 0;
+            else {
+                const int2 dw = rel(__ldg(B.q + lid[cur]), pv), dc = rel(__ldg(B.q + lid[k]), pv);
+                left = cross(dw, dc) > 0;
+            }
+            if (!left) continue;
+            if (best >= 0) {
+                int t = fcirc_filter(cb, cx, cy);
+                if (t == 0) {
+                    const uint2 qw = __ldg(B.q + lid[cur]), qb = __ldg(B.q + lid[best]),
+                                qc = __ldg(B.q + lid[k]);
+                    t = incircle_exact(rel(qw, pv), rel(qb, pv), rel(qc, pv), pv, qw, qb, qc);
+                }
+                if (t < 0) continue;
+            }
+            best = k;
+            cb = make_fcirc(wx, wy, cx, cy);
+        }
+        if (best < 0) return -1;
+        // certify: circumcircle centre (-P/2K, -Q/2K), radius |centre|, error margin far above
+        // the FP32 rounding of K, P, Q
+        const float ak = fabsf(cb.K);
+        if (!(ak > 1e-3f * cb.Ka)) return -1;
+        const float inv2k = 0.5f / cb.K;
+        const float ccx = -cb.P * inv2k, ccy = -cb.Q * inv2k;
+        const float r = sqrtf(fmaf(ccx, ccx, ccy * ccy));
+        const float err = 1e-4f * (cb.Pa + cb.Qa + (fabsf(cb.P) + fabsf(cb.Q)) * cb.Ka / ak) / ak + 64.f;
+        const float ext = r + err;
+        if (ccx - ext < -clx || ccx + ext > chx || ccy - ext < -cly || ccy + ext > chy) return -1;
+        if (2.f * ext > D * 0.9999f) return -1;
+        if (best == u0) break;
+        cur = best;
+    }
+    return n >= 3 ? n : -1;
 }
 
 // Counter-clockwise Delaunay star of slot v into nbrs[0..count).  Returns count >= 3, or
@@ -215,7 +338,12 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
 static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
 {
     const uint2 pv = __ldg(B.q + v);
-    for (int R = R0; R <= B.rmax; ++R) {
+    if (B.dmax > 0.f) {
+        const int c = star_list(B, v, pv, make_region(B, pv, R0), B.dmax, nbrs);
+        if (c != -1) return c;
+    }
+    for (int attempt = 1, R = R0; R <= B.rmax; ++attempt, R += attempt > 1 ? 1 : 0) {
+        const float dmax = 0.f;
         const Region g = make_region(B, pv, R);
         int u0 = -1;
         long long d2b = 0x7fffffffffffffffLL;
@@ -237,7 +365,7 @@ static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nb
         for (;;) {
             if (cnt == KMAX) return -PFEM_ERR_CAPACITY;
             nbrs[cnt++] = cur;
-            const int a = apex_search(B, pv, __ldg(B.q + cur), g);
+            const int a = apex_search(B, pv, __ldg(B.q + cur), g, dmax);
             if (a < 0) { ok = false; break; }
             if (a == u0) break;
             cur = a;
@@ -251,6 +379,8 @@ static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nb
 __device__ __forceinline__ int apex_of(const Bins &B, int u, int w, int R0)
 {
     const uint2 pu = __ldg(B.q + u), pw = __ldg(B.q + w);
+    const int a0 = apex_search(B, pu, pw, make_region(B, pu, R0), B.dmax);
+    if (a0 >= 0) return a0;
     for (int R = R0; R <= B.rmax; ++R) {
         const int a = apex_search(B, pu, pw, make_region(B, pu, R));
         if (a >= 0) return a;

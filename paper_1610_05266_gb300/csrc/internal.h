@@ -34,6 +34,8 @@ struct GeoArgs {
     const uint32_t *q_sorted;
     const int *cell_start;
     int R0, rmax;
+    float dmax;
+    bool tiled;                 // fused P2M may use the tiled kernel
 };
 
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,

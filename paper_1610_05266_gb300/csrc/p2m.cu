@@ -1,7 +1,7 @@
 // p2m.cu -- launchers of the particle-to-mesh kernels (fused apply, explicit weights, apply
 // from explicit weights) and of the Delaunay-star diagnostic.
 #include "internal.h"
-#include "p2m.cuh"
+#include "p2m_tiled.cuh"
 
 namespace pfem {
 
@@ -13,6 +13,7 @@ static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
     a.B.start = g.cell_start;
     a.B.nb = g.nb;
     a.B.rmax = g.rmax;
+    a.B.dmax = g.dmax;
     a.R0 = g.R0;
     a.pos = g.pos_sorted;
     a.perm = nullptr;
@@ -28,9 +29,32 @@ static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
 
 static dim3 node_grid(int n) { return dim3((n + 15) / 16, (n + 7) / 8); }
 
-template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
-static cudaError_t go(const P2MArgs &a, cudaStream_t s)
+// Nodes per tile side for the tiled kernel (0: use the per-thread kernel): the staged window
+// (tile bins + halo) must fit the shared-memory capacity and stay within half the torus.
+int tile_side(int n, int nb, long long N)
 {
+    const double bins_per_cell = (double)nb / (double)(n - 1);
+    const double ppb = (double)N / ((double)nb * nb);
+    for (int T = 16; T >= 4; T >>= 1) {
+        const int w = (int)ceil((T - 1) * bins_per_cell) + 2 + 2 * THB;
+        if (w * w <= TMAXB && 2 * w <= nb && w * w * ppb * 1.1 <= TMAXP) return T;
+    }
+    return 0;
+}
+
+template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
+static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0)
+{
+    if (!W && T > 0) {
+        auto k = k_p2m_tiled<P, V, R, S, REF, SHAPE>;
+        const int bytes = (int)sizeof(TileSmem);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        const int tx = (a.n + T - 1) / T;
+        k<<<tx * tx, TT, bytes, s>>>(a, T, tx);
+        count_launch();
+        return cudaGetLastError();
+    }
     k_p2m<P, V, R, S, REF, SHAPE, W><<<node_grid(a.n), 128, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
@@ -46,20 +70,21 @@ cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *val
     a.C = C;
     a.out = out;
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
+    const int T = g.tiled ? tile_side(g.n, g.nb, g.N) : 0;
     if (val_t == PFEM_F64) {   // positions FP64, arithmetic FP64
-        if (!q) return go<double, double, double, double, false, 0, false>(a, s);
-        return go<double, double, double, double, false, 1, false>(a, s);
+        if (!q) return go<double, double, double, double, false, 0, false>(a, s, T);
+        return go<double, double, double, double, false, 1, false>(a, s, T);
     }
     if (val_t == PFEM_F32) {   // positions FP32, arithmetic FP32
-        if (!q) return go<float, float, float, float, false, 0, false>(a, s);
-        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s);
-        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s);
-        return go<float, float, float, float, true, 1, false>(a, s);
+        if (!q) return go<float, float, float, float, false, 0, false>(a, s, T);
+        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s, T);
+        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s, T);
+        return go<float, float, float, float, true, 1, false>(a, s, T);
     }
-    if (!q) return go<float, __nv_bfloat16, float, float, false, 0, false>(a, s);
-    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s);
-    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s);
-    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s);
+    if (!q) return go<float, __nv_bfloat16, float, float, false, 0, false>(a, s, T);
+    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s, T);
+    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s, T);
+    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s, T);
 }
 
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,

@@ -127,11 +127,27 @@ __device__ __forceinline__ bool in_list(const int *lst, int n, int x)
 // particle once; sg is in star(nu), nu in star(sg)).  Calls emit(slot, coef * A_mu) for every
 // stencil member.  S is the solve precision; REFINE adds one refinement step with an FP64
 // residual.  Returns false when the moment matrix is numerically singular.
-template <typename P, typename R, typename S, bool REFINE, typename Emit>
-__device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, R> &np, int nu,
-                                             int sg, const int *st_nu, int n_nu,
-                                             const int *st_sg, int n_sg, R coef, Emit &&emit)
+// A star as a list of slots: plain slot array (per-thread path) or shared-memory indices
+// mapped to slots (tiled path).
+struct ArrStar {
+    const int *p;
+    int n;
+    __device__ __forceinline__ int operator[](int i) const { return p[i]; }
+};
+
+template <typename SA> __device__ __forceinline__ bool star_has(const SA &st, int x)
 {
+    for (int i = 0; i < st.n; ++i)
+        if (st[i] == x) return true;
+    return false;
+}
+
+template <typename P, typename R, typename S, bool REFINE, typename SA, typename Emit>
+__device__ __forceinline__ bool edge_weights_sa(const P2MArgs &a, const NodePos<P, R> &np, int nu,
+                                                int sg, const SA &st_nu, const SA &st_sg, R coef,
+                                                Emit &&emit)
+{
+    const int n_nu = st_nu.n, n_sg = st_sg.n;
     R rnx, rny, rsx, rsy;
     np.off(a.pos, nu, rnx, rny);
     np.off(a.pos, sg, rsx, rsy);
@@ -145,7 +161,7 @@ __device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, 
         for (int i = 0; i < n_nu; ++i) f(st_nu[i]);
         for (int j = 0; j < n_sg; ++j) {
             const int m = st_sg[j];
-            if (m == nu || in_list(st_nu, n_nu, m)) continue;
+            if (m == nu || star_has(st_nu, m)) continue;
             f(m);
         }
     };
@@ -198,6 +214,15 @@ __device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, 
         emit(s, coef * R(A));
     });
     return true;
+}
+
+template <typename P, typename R, typename S, bool REFINE, typename Emit>
+__device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, R> &np, int nu,
+                                             int sg, const int *st_nu, int n_nu,
+                                             const int *st_sg, int n_sg, R coef, Emit &&emit)
+{
+    return edge_weights_sa<P, R, S, REFINE>(a, np, nu, sg, ArrStar{st_nu, n_nu},
+                                            ArrStar{st_sg, n_sg}, coef, emit);
 }
 
 template <typename V> __device__ __forceinline__ V nan_of();
