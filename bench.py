@@ -363,6 +363,85 @@ def run_ours(args, world, rank, local):
     proj64.check("fp64 round trip")
     out["side"] = side
 
+    # --- batched uneven problems (256, persistent launches, tuned, CUDA graph) vs the plain
+    #     FP64 single-instance form, problem by problem
+    if not args.no_batched:
+        from paper_1610_05266_gb300 import tuner
+        from workloads import config_batched
+        probs = config_batched()
+        bpos = torch.tensor(np.concatenate([p.pos for p in probs]), dtype=torch.float32, device=dev)
+        bvals = torch.tensor(np.concatenate([p.vals for p in probs]), dtype=torch.float32, device=dev)
+        batch = P.Batch([(p.n, p.N) for p in probs], C=3, dtype=torch.float32, device=dev)
+        t0 = time.time()
+        cfg = tuner.tune_batch(batch, bpos, bvals, P.PFEM_SHAPE_QUADRATIC)
+        tune_s = time.time() - t0
+        batch.capture(bpos, bvals)
+        tb = timeit(batch.replay, reps=3)
+        code, _ = batch.status()
+        Nb = batch.N_total
+        single_ms = 0.0
+        for pb in probs:
+            pp = torch.tensor(pb.pos, dtype=torch.float64, device=dev)
+            vv = torch.tensor(pb.vals, dtype=torch.float64, device=dev)
+            pj = P.Projector(pb.n, pb.N, C=3, pos_dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            b0, b1 = ev(), ev()
+            b0.record(stream)
+            pj.build(pp)
+            mm = pj.p2m(vv)
+            pj.m2p(pp, mm)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            single_ms += b0.elapsed_time(b1)
+        out["batched"] = {"workload": "256 problems, n in 65..513, h/H in {1/4,1/2,1}, a=0.3, TG k in 1..8, C=3",
+                          "particles": Nb, "nodes": batch.nodes_total,
+                          "graph_replay_ms": tb, "mparticles_s": Nb / (tb * 1e-3) / 1e6,
+                          "dtype": "f32", "status": code, "tuned": {k: v for k, v in cfg.items() if not k.startswith("_")},
+                          "tune_s": tune_s,
+                          "fp64_single_instance_ms": single_ms,
+                          "fp64_single_instance_mparticles_s": Nb / (single_ms * 1e-3) / 1e6,
+                          "speedup_vs_fp64_single": single_ms / tb}
+        del batch, bpos, bvals
+        torch.cuda.empty_cache()
+
+    # --- precision study: 4097^2 mesh, 8192^2 particles (67M), Rayleigh-Taylor density
+    if not args.no_precision:
+        from workloads import config_precision
+        pp = config_precision()
+        ppos32 = torch.tensor(pp.pos, dtype=torch.float32, device=dev)
+        pproj = P.Projector(pp.n, pp.N, C=1, pos_dtype=torch.float32, device=dev)
+        pproj.build(ppos32)
+        variants = {}
+        rng = np.random.default_rng(1)
+        sample = rng.choice(pp.n * pp.n, 64, replace=False)
+        refs = None
+        if rank == 0 and not args.no_oracle:
+            import oracle as O
+            pcells = O.build_cells(pp.n, pp.pos.astype(np.float32).astype(np.float64))
+            refs = []
+            for node in sample:
+                J, I = divmod(int(node), pp.n)
+                idx, w, _, _ = O.node_weights(pcells, I, J, 1)
+                refs.append(w @ pp.vals[idx, 0])
+            refs = np.array(refs)
+        for vt, vname in ((torch.float32, "f32"), (torch.bfloat16, "bf16")):
+            vv = torch.tensor(pp.vals, dtype=torch.float32, device=dev).to(vt)
+            for sv, sname in ((P.PFEM_SOLVE_F64, "solve_f64"), (P.PFEM_SOLVE_F32, "solve_f32"),
+                              (P.PFEM_SOLVE_F32_REFINED, "solve_f32_refined")):
+                mesh_p = pproj.p2m(vv, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv)
+                t_v = timeit(lambda: pproj.p2m(vv, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv, out=mesh_p), reps=2)
+                ent = {"p2m_ms": t_v}
+                if refs is not None:
+                    got = mesh_p.float().cpu().numpy().reshape(-1)[sample]
+                    ent["max_rel_err_vs_fp64_oracle"] = float(np.abs(got - refs).max() / np.abs(pp.vals).max())
+                variants[f"{vname}_{sname}"] = ent
+        code, _ = pproj.status()
+        out["precision_study"] = {"workload": "4097x4097 mesh, 8192x8192 particles, RT density (C=1)",
+                                  "variants": variants, "status": code,
+                                  "error_sample": "64 random nodes, error / max|rho|"}
+        del pproj, ppos32
+        torch.cuda.empty_cache()
+
     # --- accuracy on sampled nodes and particles against the FP64 oracle
     if rank == 0 and not args.no_oracle:
         import oracle as O
@@ -413,6 +492,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="timed loop only (for ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -206,6 +206,53 @@ pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const voi
                                      const void *grad_vals, pfem_dtype val_t, void *grad_mesh,
                                      void *grad_pos, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent problems (their own mesh size, particle count and bins) processed in one
+ * launch per stage.  The caller concatenates the problems: particles of problem p occupy rows
+ * [poff_p, poff_p + N_p) of the particle arrays (pos, vals, pos_sorted, q_sorted, perm) in
+ * problem order, its bins a contiguous range of one cell_start array and its n_p^2 nodes a
+ * contiguous range of one mesh array; pfem_batch_plan_init reports the totals.  After
+ * pfem_batch_build_cells, cell_start holds global slot indices and perm global particle
+ * indices.  No paper counterpart (the paper runs one problem at a time). */
+typedef struct {
+    int32_t n;      /* mesh nodes per side (image row/column included), >= 9 */
+    int32_t nb;     /* bins per side, >= 8 (pfem_default_bins) */
+    int64_t N;      /* particles, >= 3 */
+} pfem_batch_problem;
+
+/* Bytes of the device plan for P problems. */
+size_t pfem_batch_plan_size(int32_t P);
+
+/* Build the plan (descriptors, search radii, work-item prefix tables) from P host
+ * descriptors and copy it to `plan` (device memory of pfem_batch_plan_size(P) bytes); this
+ * call synchronises.  totals[0..2] = total particles, total bins, total nodes. */
+pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, void *plan,
+                                 int64_t *totals);
+
+/* Workspace bytes of pfem_batch_build_cells / pfem_batch_project_p2m. */
+size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total);
+
+/* Binning of every problem at once (a1-a2 on the concatenated layout). */
+pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bins_total,
+                                   const void *pos, pfem_dtype pos_t, int32_t *cell_start,
+                                   int32_t *perm, void *pos_sorted, uint32_t *q_sorted, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/* P2M of every problem in one persistent launch: `blocks` blocks of 16 x tile_rows threads
+ * (tile_rows 4, 8 or 16) pull (problem, 16 x tile_rows node tile) items from a counter in ws.
+ * Values FP32 (FP32 positions) or FP64 (FP64 positions, FP64 solve). */
+pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfem_dtype pos_t,
+                                   const uint32_t *q_sorted, const int32_t *cell_start,
+                                   const int32_t *perm, int32_t C, const void *vals,
+                                   pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
+                                   void *mesh_vals, int32_t tile_rows, int32_t blocks, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/* M2P of every problem in one launch of `blocks` blocks over 4096-particle chunks. */
+pfem_status pfem_batch_interp_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int32_t C,
+                                  const void *mesh_vals, void *vals, pfem_dtype val_t,
+                                  int32_t blocks, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,48 @@ def pfem_interp_m2p_backward(n, nb, N, pos, cell_start, perm, C, mesh_vals, grad
           "pfem_interp_m2p_backward")
 
 
+def pfem_batch_plan_size(P: int) -> int:
+    return int(L.load().pfem_batch_plan_size(P))
+
+
+def pfem_batch_plan_init(problems, plan: torch.Tensor):
+    """problems: list of (n, nb, N).  Returns (N_total, bins_total, nodes_total)."""
+    arr = (L.BatchProblem * len(problems))(*[L.BatchProblem(n, nb, N) for n, nb, N in problems])
+    tot = (ctypes.c_int64 * 3)()
+    check(L.load().pfem_batch_plan_init(len(problems), ctypes.cast(arr, ctypes.c_void_p), ptr(plan),
+                                        ctypes.cast(tot, ctypes.POINTER(ctypes.c_int64))),
+          "pfem_batch_plan_init")
+    return int(tot[0]), int(tot[1]), int(tot[2])
+
+
+def pfem_batch_workspace_size(N_total: int, bins_total: int) -> int:
+    return int(L.load().pfem_batch_workspace_size(N_total, bins_total))
+
+
+def pfem_batch_build_cells(plan, N_total, bins_total, pos, cell_start, perm, pos_sorted, q_sorted,
+                           ws, stream=None):
+    check(L.load().pfem_batch_build_cells(ptr(plan), N_total, bins_total, ptr(pos),
+                                          dtype_code(pos.dtype), ptr(cell_start), ptr(perm),
+                                          ptr(pos_sorted), ptr(q_sorted), ptr(ws),
+                                          ws.numel() * ws.element_size(), stream_ptr(stream)),
+          "pfem_batch_build_cells")
+
+
+def pfem_batch_project_p2m(plan, pos_sorted, q_sorted, cell_start, perm, C, vals, shape, solve,
+                           mesh_vals, tile_rows, blocks, ws, stream=None):
+    check(L.load().pfem_batch_project_p2m(ptr(plan), ptr(pos_sorted), dtype_code(pos_sorted.dtype),
+                                          ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
+                                          dtype_code(vals.dtype), shape, solve, ptr(mesh_vals),
+                                          tile_rows, blocks, ptr(ws), ws.numel() * ws.element_size(),
+                                          stream_ptr(stream)), "pfem_batch_project_p2m")
+
+
+def pfem_batch_interp_m2p(plan, pos, C, mesh_vals, vals, blocks, stream=None):
+    check(L.load().pfem_batch_interp_m2p(ptr(plan), ptr(pos), dtype_code(pos.dtype), C,
+                                         ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype), blocks,
+                                         stream_ptr(stream)), "pfem_batch_interp_m2p")
+
+
 @dataclass
 class Cells:
     """Device buffers of one binned particle set (output of pfem_build_cells)."""
@@ -246,3 +288,84 @@ class Projector:
         code, detail = self.status(stream)
         if code != 0:
             raise PfemError(code, f"{what} (first failure at index {detail})")
+
+
+class Batch:
+    """Device buffers and plan for many independent problems processed together.
+
+    `sizes` is a list of (n, N) per problem; particle rows of problem p are
+    [offsets[p], offsets[p+1]) of the concatenated pos/vals arrays, and its mesh is
+    mesh_view(p) of the concatenated mesh output.
+    """
+
+    def __init__(self, sizes, C: int, dtype=torch.float32, device="cuda"):
+        self.device = torch.device(device)
+        self.C, self.dtype = C, dtype
+        self.problems = [(n, pfem_default_bins(n, N), N) for n, N in sizes]
+        self.plan = torch.zeros((pfem_batch_plan_size(len(sizes)) + 7) // 8, dtype=torch.float64,
+                                device=self.device)
+        self.N_total, self.bins_total, self.nodes_total = pfem_batch_plan_init(self.problems, self.plan)
+        dev = self.device
+        self.cell_start = torch.empty(self.bins_total + 1, dtype=torch.int32, device=dev)
+        self.perm = torch.empty(self.N_total, dtype=torch.int32, device=dev)
+        self.pos_sorted = torch.empty((self.N_total, 2), dtype=dtype, device=dev)
+        self.q_sorted = torch.empty((self.N_total, 2), dtype=torch.int32, device=dev)
+        wsb = pfem_batch_workspace_size(self.N_total, self.bins_total)
+        self.ws = torch.zeros((wsb + 7) // 8, dtype=torch.float64, device=dev)
+        self.mesh = torch.empty((self.nodes_total, C), dtype=dtype, device=dev)
+        self.back = torch.empty((self.N_total, C), dtype=dtype, device=dev)
+        offs, noffs = [0], [0]
+        for n, _, N in self.problems:
+            offs.append(offs[-1] + N)
+            noffs.append(noffs[-1] + n * n)
+        self.offsets, self.node_offsets = offs, noffs
+        self.config = {"tile_rows": 8, "p2m_blocks": 152 * 8, "m2p_blocks": 152 * 16}
+        self.graph = None
+
+    def mesh_view(self, p: int) -> torch.Tensor:
+        n = self.problems[p][0]
+        return self.mesh[self.node_offsets[p]: self.node_offsets[p + 1]].view(n, n, self.C)
+
+    def build(self, pos, stream=None):
+        pfem_batch_build_cells(self.plan, self.N_total, self.bins_total, pos, self.cell_start,
+                               self.perm, self.pos_sorted, self.q_sorted, self.ws, stream)
+
+    def p2m(self, vals, shape=PFEM_SHAPE_QUADRATIC, solve=None, tile_rows=None, blocks=None,
+            stream=None):
+        if solve is None:
+            solve = PFEM_SOLVE_F64 if vals.dtype == torch.float64 else PFEM_SOLVE_F32
+        pfem_batch_project_p2m(self.plan, self.pos_sorted, self.q_sorted, self.cell_start,
+                               self.perm, self.C, vals, shape, solve, self.mesh,
+                               tile_rows or self.config["tile_rows"],
+                               blocks or self.config["p2m_blocks"], self.ws, stream)
+        return self.mesh
+
+    def m2p(self, pos, blocks=None, stream=None):
+        pfem_batch_interp_m2p(self.plan, pos, self.C, self.mesh, self.back,
+                              blocks or self.config["m2p_blocks"], stream)
+        return self.back
+
+    def round_trip(self, pos, vals, shape=PFEM_SHAPE_QUADRATIC, solve=None, stream=None):
+        self.build(pos, stream)
+        self.p2m(vals, shape, solve, stream=stream)
+        return self.m2p(pos, stream=stream)
+
+    def capture(self, pos, vals, shape=PFEM_SHAPE_QUADRATIC, solve=None):
+        """Capture build + P2M + M2P (tuned configuration) in a CUDA graph; replay() runs it."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.round_trip(pos, vals, shape, solve, stream=s)       # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.round_trip(pos, vals, shape, solve)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.back
+
+    def status(self, stream=None):
+        return pfem_read_status(self.ws, stream)

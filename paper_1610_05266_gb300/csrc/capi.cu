@@ -21,11 +21,15 @@ WsLayout ws_layout(int n, int nb, long long N, int C)
 {
     (void)n;
     (void)C;
+    return ws_layout_bins((long long)nb * nb, N);
+}
+
+WsLayout ws_layout_bins(long long nbins, long long N)
+{
     WsLayout L;
     size_t off = 0;
     L.status = off;
     off += 256;
-    const long long nbins = (long long)nb * nb;
     L.count = off;
     off = align256(off + sizeof(int) * (size_t)(nbins + 1));
     L.key = off;
@@ -63,6 +67,14 @@ static void radii(int32_t nb, int64_t N, int *R0, int *rmax)
     *rmax = rm;
 }
 
+namespace pfem {
+void radii_for(int nb, long long N, int *R0, int *rmax, float *dmax)
+{
+    radii(nb, N, R0, rmax);
+    *dmax = (float)std::fmin(2.5 * 4294967296.0 / std::sqrt((double)N), 1073741824.0);
+}
+}  // namespace pfem
+
 static bool make_geo(int32_t n, int32_t nb, int64_t N, const void *pos_sorted, pfem_dtype pos_t,
                      const uint32_t *q_sorted, const int32_t *cell_start, GeoArgs *g)
 {
@@ -75,9 +87,9 @@ static bool make_geo(int32_t n, int32_t nb, int64_t N, const void *pos_sorted, p
     g->pos_t = pos_t;
     g->q_sorted = q_sorted;
     g->cell_start = cell_start;
-    radii(nb, N, &g->R0, &g->rmax);
-    // distance cutoff of the first star attempt: 2.5 mean particle spacings (fixed point)
-    g->dmax = (float)std::fmin(2.5 * 4294967296.0 / std::sqrt((double)N), 1073741824.0);
+    // first search radius, largest radius, and the distance cutoff of the first star attempt
+    // (2.5 mean particle spacings, fixed point)
+    radii_for(nb, N, &g->R0, &g->rmax, &g->dmax);
     // The shared-memory tiled P2M is opt-in: on the jittered-lattice workloads it measured
     // slower than the per-thread kernel (the cost is in the divergent star search, not memory).
     g->tiled = getenv("PFEM_TILED") != nullptr;
@@ -279,6 +291,76 @@ pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const voi
     return from_cuda(launch_m2p_backward(n, nb, N, pos, pos_t, cell_start, perm, C, mesh_vals,
                                          grad_vals, val_t, grad_mesh, grad_pos,
                                          (cudaStream_t)stream));
+}
+
+size_t pfem_batch_plan_size(int32_t P)
+{
+    return P < 1 ? 0 : batch_plan_bytes(P);
+}
+
+pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, void *plan,
+                                 int64_t *totals)
+{
+    if (P < 1 || !problems || !plan || !totals) return PFEM_ERR_INVALID_ARG;
+    long long Nt = 0, bt = 0, nt = 0;
+    const int st = batch_plan_build(P, problems, plan, &Nt, &bt, &nt);
+    if (st != PFEM_OK) return (pfem_status)st;
+    totals[0] = Nt;
+    totals[1] = bt;
+    totals[2] = nt;
+    return PFEM_OK;
+}
+
+size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total)
+{
+    if (N_total < 0 || bins_total < 1) return 0;
+    return ws_layout_bins(bins_total, N_total).total;
+}
+
+pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bins_total,
+                                   const void *pos, pfem_dtype pos_t, int32_t *cell_start,
+                                   int32_t *perm, void *pos_sorted, uint32_t *q_sorted, void *ws,
+                                   size_t ws_bytes, void *stream)
+{
+    if (!plan || !pos || !cell_start || !perm || !pos_sorted || !q_sorted || !ws) return PFEM_ERR_INVALID_ARG;
+    if (N_total < 1 || N_total >= (1LL << 31) || bins_total < 1 || bins_total >= (1LL << 31)) return PFEM_ERR_INVALID_ARG;
+    if (pos_t != PFEM_F64 && pos_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
+    const WsLayout L = ws_layout_bins(bins_total, N_total);
+    if (ws_bytes < L.total) return PFEM_ERR_WORKSPACE;
+    return from_cuda(launch_batch_build_cells(plan, N_total, bins_total, pos, pos_t, cell_start, perm,
+                                              pos_sorted, q_sorted, L, ws, (cudaStream_t)stream));
+}
+
+pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfem_dtype pos_t,
+                                   const uint32_t *q_sorted, const int32_t *cell_start,
+                                   const int32_t *perm, int32_t C, const void *vals,
+                                   pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
+                                   void *mesh_vals, int32_t tile_rows, int32_t blocks, void *ws,
+                                   size_t ws_bytes, void *stream)
+{
+    if (!plan || !pos_sorted || !q_sorted || !cell_start || !perm || !vals || !mesh_vals || !ws)
+        return PFEM_ERR_INVALID_ARG;
+    if (C < 1 || C > 8 || blocks < 1 || ws_bytes < 256) return PFEM_ERR_INVALID_ARG;
+    const int sidx = tile_rows == 4 ? 0 : tile_rows == 8 ? 1 : tile_rows == 16 ? 2 : -1;
+    if (sidx < 0) return PFEM_ERR_INVALID_ARG;
+    if (shape != PFEM_SHAPE_LINEAR && shape != PFEM_SHAPE_QUADRATIC) return PFEM_ERR_INVALID_ARG;
+    if (val_t == PFEM_F64 && (pos_t != PFEM_F64 || solve != PFEM_SOLVE_F64)) return PFEM_ERR_INVALID_ARG;
+    if (val_t == PFEM_F32 && pos_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
+    if (val_t == PFEM_BF16) return PFEM_ERR_INVALID_ARG;
+    if (solve < PFEM_SOLVE_F64 || solve > PFEM_SOLVE_F32_REFINED) return PFEM_ERR_INVALID_ARG;
+    return from_cuda(launch_batch_p2m(plan, pos_sorted, q_sorted, cell_start, perm, C, vals, val_t,
+                                      shape, solve, mesh_vals, sidx, blocks, ws, (cudaStream_t)stream));
+}
+
+pfem_status pfem_batch_interp_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int32_t C,
+                                  const void *mesh_vals, void *vals, pfem_dtype val_t,
+                                  int32_t blocks, void *stream)
+{
+    if (!plan || !pos || !mesh_vals || !vals || C < 1 || C > 8 || blocks < 1) return PFEM_ERR_INVALID_ARG;
+    if (!((val_t == PFEM_F64 && pos_t == PFEM_F64) || (val_t == PFEM_F32 && pos_t == PFEM_F32)))
+        return PFEM_ERR_INVALID_ARG;
+    return from_cuda(launch_batch_m2p(plan, pos, pos_t, C, mesh_vals, vals, val_t, blocks,
+                                      (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -153,6 +153,32 @@ static unsigned grid_for(long long work, int threads)
     return (unsigned)b;
 }
 
+// Scatter to slot start + rank, order each bin by original index, gather sorted positions.
+template <typename P>
+static cudaError_t sort_gather_t(long long nbins, long long N, const P *pos, const int *key,
+                                 const int *rank, const int *cell_start, int *perm, P *pos_sorted,
+                                 uint2 *q_sorted, cudaStream_t s)
+{
+    if (N > 0) {
+        k_scatter<<<grid_for(N, 256), 256, 0, s>>>(N, key, rank, cell_start, perm);
+        k_sort_bins<<<grid_for(nbins, 128), 128, 0, s>>>(nbins, cell_start, perm);
+        k_gather<P><<<grid_for(N, 256), 256, 0, s>>>(N, pos, perm, pos_sorted, q_sorted);
+        count_launch(3);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_gather(long long nbins, long long N, const void *pos, pfem_dtype pos_t,
+                               const int *key, const int *rank, const int *cell_start, int *perm,
+                               void *pos_sorted, uint32_t *q_sorted, cudaStream_t s)
+{
+    if (pos_t == PFEM_F64)
+        return sort_gather_t<double>(nbins, N, (const double *)pos, key, rank, cell_start, perm,
+                                     (double *)pos_sorted, (uint2 *)q_sorted, s);
+    return sort_gather_t<float>(nbins, N, (const float *)pos, key, rank, cell_start, perm,
+                                (float *)pos_sorted, (uint2 *)q_sorted, s);
+}
+
 template <typename P>
 static cudaError_t build_cells_t(int nb, long long N, const P *pos, int *cell_start, int *perm,
                                  P *pos_sorted, uint2 *q_sorted, const WsLayout &L, char *ws,
@@ -171,13 +197,7 @@ static cudaError_t build_cells_t(int nb, long long N, const P *pos, int *cell_st
     }
     e = scan_exclusive(count, cell_start, nbins + 1, scr, s);
     if (e != cudaSuccess) return e;
-    if (N > 0) {
-        k_scatter<<<grid_for(N, 256), 256, 0, s>>>(N, key, rank, cell_start, perm);
-        k_sort_bins<<<grid_for(nbins, 128), 128, 0, s>>>(nbins, cell_start, perm);
-        k_gather<P><<<grid_for(N, 256), 256, 0, s>>>(N, pos, perm, pos_sorted, q_sorted);
-        count_launch(3);
-    }
-    return cudaGetLastError();
+    return sort_gather_t<P>(nbins, N, pos, key, rank, cell_start, perm, pos_sorted, q_sorted, s);
 }
 
 cudaError_t launch_build_cells(int nb, long long N, const void *pos, pfem_dtype pos_t,

@@ -19,6 +19,24 @@ struct WsLayout {
 };
 
 WsLayout ws_layout(int n, int nb, long long N, int C);
+WsLayout ws_layout_bins(long long nbins, long long N);
+cudaError_t launch_sort_gather(long long nbins, long long N, const void *pos, pfem_dtype pos_t,
+                               const int *key, const int *rank, const int *cell_start, int *perm,
+                               void *pos_sorted, uint32_t *q_sorted, cudaStream_t s);
+size_t batch_plan_bytes(int P);
+int batch_plan_build(int P, const pfem_batch_problem *probs, void *plan_dev, long long *N_total,
+                     long long *bins_total, long long *nodes_total);
+cudaError_t launch_batch_build_cells(const void *plan, long long Ntot, long long bins_total,
+                                     const void *pos, pfem_dtype pos_t, int *cell_start, int *perm,
+                                     void *pos_sorted, uint32_t *q_sorted, const WsLayout &L,
+                                     void *ws, cudaStream_t s);
+cudaError_t launch_batch_p2m(const void *plan, const void *pos_sorted, const uint32_t *q_sorted,
+                             const int *cell_start, const int *perm, int C, const void *vals,
+                             pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *mesh,
+                             int shape_idx, int blocks, void *ws, cudaStream_t s);
+cudaError_t launch_batch_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int C,
+                             const void *mesh, void *vals, pfem_dtype val_t, int blocks,
+                             cudaStream_t s);
 size_t scan_scratch_ints(long long n);
 cudaError_t scan_exclusive(const int *in, int *out, long long n, int *scratch, cudaStream_t s);
 
