@@ -259,8 +259,7 @@ __device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
 static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
                                              float D, int *nbrs)
 {
-    float lx[KL], ly[KL];
-    int lid[KL];
+    float4 L[KL];                   // (x, y, |c|^2, slot as bits) relative to v
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
     bool dup = false, over = false;
@@ -269,11 +268,12 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
         if (s == v) return;
         const int2 d = rel(__ldg(B.q + s), pv);
         const float fx = (float)d.x, fy = (float)d.y;
-        if (fmaf(fx, fx, fy * fy) > D2) return;
+        const float l = fmaf(fx, fx, fy * fy);
+        if (l > D2) return;
         const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
         dup |= d2 == 0;
         if (cnt == KL) { over = true; return; }
-        lx[cnt] = fx; ly[cnt] = fy; lid[cnt] = s;
+        L[cnt] = make_float4(fx, fy, l, __int_as_float(s));
         if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; }
         ++cnt;
     });
@@ -283,38 +283,50 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
     int cur = u0, n = 0;
     for (;;) {
         if (n == KMAX) return -PFEM_ERR_CAPACITY;
-        nbrs[n++] = lid[cur];
-        const float wx = lx[cur], wy = ly[cur];
+        const float4 W = L[cur];
+        const int wslot = __float_as_int(W.w);
+        nbrs[n++] = wslot;
+        const float wx = W.x, wy = W.y, lw = W.z;
         int best = -1;
         FCirc cb;
         cb.K = cb.P = cb.Q = cb.Ka = cb.Pa = cb.Qa = 0.f;
+        float lbx = 0.f, lby = 0.f, lbl = 0.f;
         for (int k = 0; k < cnt; ++k) {
-            if (k == cur) continue;
-            const float cx = lx[k], cy = ly[k];
-            // orientation of (v, w, c): FP32 filter, exact on ties
-            const float o1 = wx * cy, o2 = wy * cx;
+            const float4 c = L[k];
+            // orientation of (v, w, c): FP32 filter
+            const float o1 = wx * c.y, o2 = wy * c.x;
             const float o = o1 - o2;
             const float ob = 4.76837158203125e-07f * (fabsf(o1) + fabsf(o2));
-            int left;
-            if (o > ob) left = 1;
-            else if (o < -ob) left = 0;
-            else {
-                const int2 dw = rel(__ldg(B.q + lid[cur]), pv), dc = rel(__ldg(B.q + lid[k]), pv);
+            bool left = o > ob;
+            if (fabsf(o) <= ob && k != cur) {            // rare: decide exactly
+                const int2 dw = rel(__ldg(B.q + wslot), pv);
+                const int2 dc = rel(__ldg(B.q + __float_as_int(c.w)), pv);
                 left = cross(dw, dc) > 0;
             }
             if (!left) continue;
             if (best >= 0) {
-                int t = fcirc_filter(cb, cx, cy);
-                if (t == 0) {
-                    const uint2 qw = __ldg(B.q + lid[cur]), qb = __ldg(B.q + lid[best]),
-                                qc = __ldg(B.q + lid[k]);
+                // inside circle(v, w, best)?  det = K l + P x + Q y < 0
+                const float det = fmaf(cb.K, c.z, fmaf(cb.P, c.x, cb.Q * c.y));
+                const float mag = fmaf(cb.Ka, c.z, fmaf(cb.Pa, fabsf(c.x), cb.Qa * fabsf(c.y)));
+                const float bnd = 1.9073486328125e-06f * mag;
+                int t = det < -bnd ? 1 : (det > bnd ? -1 : 0);
+                if (t == 0) {                              // rare: decide exactly
+                    const uint2 qw = __ldg(B.q + wslot), qb = __ldg(B.q + __float_as_int(L[best].w)),
+                                qc = __ldg(B.q + __float_as_int(c.w));
                     t = incircle_exact(rel(qw, pv), rel(qb, pv), rel(qc, pv), pv, qw, qb, qc);
                 }
                 if (t < 0) continue;
             }
             best = k;
-            cb = make_fcirc(wx, wy, cx, cy);
+            lbx = c.x; lby = c.y; lbl = c.z;
+            // circle through v, w, c: K = w x c, P = |c|^2 wy - |w|^2 cy, Q = |w|^2 cx - |c|^2 wx
+            const float k1 = wx * c.y, k2 = wy * c.x;
+            const float t1 = c.z * wy, t2 = lw * c.y, t3 = lw * c.x, t4 = c.z * wx;
+            cb.K = k1 - k2;  cb.Ka = fabsf(k1) + fabsf(k2);
+            cb.P = t1 - t2;  cb.Pa = fabsf(t1) + fabsf(t2);
+            cb.Q = t3 - t4;  cb.Qa = fabsf(t3) + fabsf(t4);
         }
+        (void)lbx; (void)lby; (void)lbl;
         if (best < 0) return -1;
         // certify: circumcircle centre (-P/2K, -Q/2K), radius |centre|, error margin far above
         // the FP32 rounding of K, P, Q

@@ -225,6 +225,97 @@ __device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, 
                                             ArrStar{st_sg, n_sg}, coef, emit);
 }
 
+// Quadratic weights of one node over its distinct particles U = T + stars of T's vertices:
+// offsets are loaded once per particle, each edge's stencil is a bit mask over U, and
+// w_u = lambda_u [u in T] + sum_e 2 lambda_nu lambda_sg A_{u e} accumulates per particle.
+// Calls emit(slot, w) once per particle of U.  Returns 0, or -PFEM_ERR_* (singular moment
+// matrix, or more than 32 distinct particles).
+constexpr int UMAX = 32;
+
+template <typename P, typename R, typename S, bool REFINE, typename SA, typename Emit>
+__device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
+                                              const int tri[3], const SA *st, const R lam[3],
+                                              Emit &&emit)
+{
+    int us[UMAX];
+    R ux[UMAX], uy[UMAX], uw[UMAX];
+    int nu = 0;
+    bool over = false;
+    auto add = [&](int s) -> int {
+        for (int i = 0; i < nu; ++i)
+            if (us[i] == s) return i;
+        if (nu == UMAX) { over = true; return 0; }
+        us[nu] = s;
+        np.off(a.pos, s, ux[nu], uy[nu]);
+        uw[nu] = R(0);
+        return nu++;
+    };
+    unsigned vm[3];
+    int vi[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        vi[e] = add(tri[e]);
+        uw[vi[e]] += lam[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        unsigned m = 1u << vi[e];
+        for (int i = 0; i < st[e].n; ++i) m |= 1u << add(st[e][i]);
+        vm[e] = m;
+    }
+    if (over) return -PFEM_ERR_CAPACITY;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int f = e == 2 ? 0 : e + 1;
+        const unsigned mask = vm[e] | vm[f];
+        const S rnx = S(ux[vi[e]]), rny = S(uy[vi[e]]), rsx = S(ux[vi[f]]), rsy = S(uy[vi[f]]);
+        const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
+        const S ex = rnx - rsx, ey = rny - rsy;
+        const S inv = S(1) / sqrt(ex * ex + ey * ey);
+        Moment<S> M;
+        M.zero();
+        for (unsigned m = mask; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            M.add((S(ux[i]) - mx) * inv, (S(uy[i]) - my) * inv);
+        }
+        if (!M.factor(SolveTol<S>::v)) return -PFEM_ERR_DEGENERATE;
+        const S tx = ex * inv, ty = ey * inv;
+        const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
+        S y[6];
+        M.solve(b, y);
+        if (REFINE) {
+            double r[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[k] = (double)b[k];
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int i = __ffs(m) - 1;
+                const double X = (double)((S(ux[i]) - mx) * inv), Y = (double)((S(uy[i]) - my) * inv);
+                const double p[6] = {1.0, X, Y, X * X, X * Y, Y * Y};
+                double t = 0.0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) t = fma(p[k], (double)y[k], t);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) r[k] = fma(-p[k], t, r[k]);
+            }
+            S rs[6], dy[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rs[k] = (S)r[k];
+            M.solve(rs, dy);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] += dy[k];
+        }
+        const R coef = R(2) * lam[e] * lam[f];
+        for (unsigned m = mask; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            const S x = (S(ux[i]) - mx) * inv, yv = (S(uy[i]) - my) * inv;
+            const S A = y[0] + x * y[1] + yv * y[2] + x * x * y[3] + x * yv * y[4] + yv * yv * y[5];
+            uw[i] = fma(coef, R(A), uw[i]);
+        }
+    }
+    for (int i = 0; i < nu; ++i) emit(us[i], uw[i]);
+    return 0;
+}
+
 template <typename V> __device__ __forceinline__ V nan_of();
 template <> __device__ __forceinline__ float nan_of<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double nan_of<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -275,14 +366,12 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
                 if (c < a.C) acc[c] = fma(wgt, v[c], acc[c]);
         };
         if (st == 0) {
-            for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
-            if (SHAPE == PFEM_SHAPE_QUADRATIC)
-                for (int e = 0; e < 3 && st == 0; ++e) {
-                    const int f = e == 2 ? 0 : e + 1;
-                    if (!edge_weights<P, R, S, REFINE>(a, np, tri[e], tri[f], stars[e], ns[e],
-                                                       stars[f], ns[f], R(2) * lam[e] * lam[f], emit))
-                        st = -PFEM_ERR_DEGENERATE;
-                }
+            if (SHAPE == PFEM_SHAPE_QUADRATIC) {
+                const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
+                st = node_quadratic<P, R, S, REFINE>(a, np, tri, sa, lam, emit);
+            } else {
+                for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
+            }
         }
         if (st != 0) {
             record_error(a.status, -st, node);
@@ -302,14 +391,12 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
             else over = true;
         };
         if (st == 0) {
-            for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
-            if (SHAPE == PFEM_SHAPE_QUADRATIC)
-                for (int e = 0; e < 3 && st == 0; ++e) {
-                    const int f = e == 2 ? 0 : e + 1;
-                    if (!edge_weights<P, R, S, REFINE>(a, np, tri[e], tri[f], stars[e], ns[e],
-                                                       stars[f], ns[f], R(2) * lam[e] * lam[f], emit))
-                        st = -PFEM_ERR_DEGENERATE;
-                }
+            if (SHAPE == PFEM_SHAPE_QUADRATIC) {
+                const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
+                st = node_quadratic<P, R, S, REFINE>(a, np, tri, sa, lam, emit);
+            } else {
+                for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
+            }
             if (over && st == 0) st = -PFEM_ERR_CAPACITY;
         }
         if (st != 0) {

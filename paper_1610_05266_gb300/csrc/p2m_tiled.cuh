@@ -432,19 +432,17 @@ __global__ void __launch_bounds__(TT, 2) k_p2m_tiled(P2MArgs a, int T, int tiles
         for (int c = 0; c < 8; ++c)
             if (c < a.C) acc[c] = fma(wgt, v[c], acc[c]);
     };
-    for (int e = 0; e < 3; ++e) emit(gt[e], lam[e]);
-    bool ok = true;
+    int err = 0;
     if (SHAPE == PFEM_SHAPE_QUADRATIC) {
-        for (int e = 0; e < 3 && ok; ++e) {
-            const int f = e == 2 ? 0 : e + 1;
-            const SmemStar sa{S.star[sw[e]], S.gslot, S.scount[sw[e]]};
-            const SmemStar sb{S.star[sw[f]], S.gslot, S.scount[sw[f]]};
-            ok = edge_weights_sa<P, R, SV, REFINE>(a, np, gt[e], gt[f], sa, sb,
-                                                  R(2) * lam[e] * lam[f], emit);
-        }
+        const SmemStar sa[3] = {{S.star[sw[0]], S.gslot, S.scount[sw[0]]},
+                                {S.star[sw[1]], S.gslot, S.scount[sw[1]]},
+                                {S.star[sw[2]], S.gslot, S.scount[sw[2]]}};
+        err = node_quadratic<P, R, SV, REFINE>(a, np, gt, sa, lam, emit);
+    } else {
+        for (int e = 0; e < 3; ++e) emit(gt[e], lam[e]);
     }
-    if (!ok) {
-        record_error(a.status, PFEM_ERR_DEGENERATE, node);
+    if (err) {
+        record_error(a.status, -err, node);
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
     }
