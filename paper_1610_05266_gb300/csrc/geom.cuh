@@ -227,7 +227,7 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
 // circumcircle lies inside the searched region and within distance D of v, so no particle
 // left out of the list can be inside it.
 
-constexpr int KL = 24;   // list capacity
+constexpr int KL = 28;   // list capacity (about 20 particles lie within the cutoff)
 
 struct FCirc {
     float K, P, Q, Ka, Pa, Qa;
@@ -259,7 +259,8 @@ __device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
 static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
                                              float D, int *nbrs)
 {
-    float4 L[KL];                   // (x, y, |c|^2, slot as bits) relative to v
+    float2 L[KL];                   // (x, y) relative to v
+    int Ls[KL];                     // slots
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
     bool dup = false, over = false;
@@ -273,7 +274,8 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
         const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
         dup |= d2 == 0;
         if (cnt == KL) { over = true; return; }
-        L[cnt] = make_float4(fx, fy, l, __int_as_float(s));
+        L[cnt] = make_float2(fx, fy);
+        Ls[cnt] = s;
         if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; }
         ++cnt;
     });
@@ -283,16 +285,17 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
     int cur = u0, n = 0;
     for (;;) {
         if (n == KMAX) return -PFEM_ERR_CAPACITY;
-        const float4 W = L[cur];
-        const int wslot = __float_as_int(W.w);
+        const float2 W = L[cur];
+        const int wslot = Ls[cur];
         nbrs[n++] = wslot;
-        const float wx = W.x, wy = W.y, lw = W.z;
+        const float wx = W.x, wy = W.y, lw = fmaf(wx, wx, wy * wy);
         int best = -1;
         FCirc cb;
         cb.K = cb.P = cb.Q = cb.Ka = cb.Pa = cb.Qa = 0.f;
         float lbx = 0.f, lby = 0.f, lbl = 0.f;
         for (int k = 0; k < cnt; ++k) {
-            const float4 c = L[k];
+            const float2 c2 = L[k];
+            const float4 c = make_float4(c2.x, c2.y, fmaf(c2.x, c2.x, c2.y * c2.y), 0.f);
             // orientation of (v, w, c): FP32 filter
             const float o1 = wx * c.y, o2 = wy * c.x;
             const float o = o1 - o2;
@@ -300,7 +303,7 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
             bool left = o > ob;
             if (fabsf(o) <= ob && k != cur) {            // rare: decide exactly
                 const int2 dw = rel(__ldg(B.q + wslot), pv);
-                const int2 dc = rel(__ldg(B.q + __float_as_int(c.w)), pv);
+                const int2 dc = rel(__ldg(B.q + Ls[k]), pv);
                 left = cross(dw, dc) > 0;
             }
             if (!left) continue;
@@ -311,8 +314,8 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
                 const float bnd = 1.9073486328125e-06f * mag;
                 int t = det < -bnd ? 1 : (det > bnd ? -1 : 0);
                 if (t == 0) {                              // rare: decide exactly
-                    const uint2 qw = __ldg(B.q + wslot), qb = __ldg(B.q + __float_as_int(L[best].w)),
-                                qc = __ldg(B.q + __float_as_int(c.w));
+                    const uint2 qw = __ldg(B.q + wslot), qb = __ldg(B.q + Ls[best]),
+                                qc = __ldg(B.q + Ls[k]);
                     t = incircle_exact(rel(qw, pv), rel(qb, pv), rel(qc, pv), pv, qw, qb, qc);
                 }
                 if (t < 0) continue;

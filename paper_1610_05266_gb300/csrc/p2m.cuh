@@ -230,15 +230,17 @@ __device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, 
 // w_u = lambda_u [u in T] + sum_e 2 lambda_nu lambda_sg A_{u e} accumulates per particle.
 // Calls emit(slot, w) once per particle of U.  Returns 0, or -PFEM_ERR_* (singular moment
 // matrix, or more than 32 distinct particles).
-constexpr int UMAX = 32;
+constexpr int UMAX = 24;
 
 template <typename P, typename R, typename S, bool REFINE, typename SA, typename Emit>
 __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
                                               const int tri[3], const SA *st, const R lam[3],
                                               Emit &&emit)
 {
+    // Only the slots and weights are kept per thread: offsets are re-read from the positions,
+    // which neighbouring nodes share in L1, instead of being copied into thread-private memory.
     int us[UMAX];
-    R ux[UMAX], uy[UMAX], uw[UMAX];
+    R uw[UMAX];
     int nu = 0;
     bool over = false;
     auto add = [&](int s) -> int {
@@ -246,9 +248,14 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
             if (us[i] == s) return i;
         if (nu == UMAX) { over = true; return 0; }
         us[nu] = s;
-        np.off(a.pos, s, ux[nu], uy[nu]);
         uw[nu] = R(0);
         return nu++;
+    };
+    auto offset = [&](int i, S &x, S &y) {
+        R dx, dy;
+        np.off(a.pos, us[i], dx, dy);
+        x = S(dx);
+        y = S(dy);
     };
     unsigned vm[3];
     int vi[3];
@@ -268,7 +275,9 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
     for (int e = 0; e < 3; ++e) {
         const int f = e == 2 ? 0 : e + 1;
         const unsigned mask = vm[e] | vm[f];
-        const S rnx = S(ux[vi[e]]), rny = S(uy[vi[e]]), rsx = S(ux[vi[f]]), rsy = S(uy[vi[f]]);
+        S rnx, rny, rsx, rsy;
+        offset(vi[e], rnx, rny);
+        offset(vi[f], rsx, rsy);
         const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
         const S ex = rnx - rsx, ey = rny - rsy;
         const S inv = S(1) / sqrt(ex * ex + ey * ey);
@@ -276,7 +285,9 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         M.zero();
         for (unsigned m = mask; m; m &= m - 1) {
             const int i = __ffs(m) - 1;
-            M.add((S(ux[i]) - mx) * inv, (S(uy[i]) - my) * inv);
+            S ox, oy;
+            offset(i, ox, oy);
+            M.add((ox - mx) * inv, (oy - my) * inv);
         }
         if (!M.factor(SolveTol<S>::v)) return -PFEM_ERR_DEGENERATE;
         const S tx = ex * inv, ty = ey * inv;
@@ -289,7 +300,9 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
             for (int k = 0; k < 6; ++k) r[k] = (double)b[k];
             for (unsigned m = mask; m; m &= m - 1) {
                 const int i = __ffs(m) - 1;
-                const double X = (double)((S(ux[i]) - mx) * inv), Y = (double)((S(uy[i]) - my) * inv);
+                S ox, oy;
+                offset(i, ox, oy);
+                const double X = (double)((ox - mx) * inv), Y = (double)((oy - my) * inv);
                 const double p[6] = {1.0, X, Y, X * X, X * Y, Y * Y};
                 double t = 0.0;
 #pragma unroll
@@ -307,7 +320,9 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         const R coef = R(2) * lam[e] * lam[f];
         for (unsigned m = mask; m; m &= m - 1) {
             const int i = __ffs(m) - 1;
-            const S x = (S(ux[i]) - mx) * inv, yv = (S(uy[i]) - my) * inv;
+            S ox, oy;
+            offset(i, ox, oy);
+            const S x = (ox - mx) * inv, yv = (oy - my) * inv;
             const S A = y[0] + x * y[1] + yv * y[2] + x * x * y[3] + x * yv * y[4] + yv * yv * y[5];
             uw[i] = fma(coef, R(A), uw[i]);
         }
