@@ -75,11 +75,13 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Largest value over the replicas (timing is the slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -148,6 +150,8 @@ def oracle_baseline(pr, node_sample: int, particle_sample: int, threads: int):
     """Time the FP64 oracle on a bounded sample of the workload; scale to the whole job."""
     import oracle as O
     n, N = pr.n, pr.N
+    node_sample = min(node_sample, n * n)
+    particle_sample = min(particle_sample, N)
     pos = np.ascontiguousarray(pr.pos.astype(np.float32).astype(np.float64))
     vals = np.ascontiguousarray(pr.vals)
     t0 = time.perf_counter()
@@ -168,11 +172,11 @@ def oracle_baseline(pr, node_sample: int, particle_sample: int, threads: int):
                         "m2p_particles": particle_sample, "m2p_s": t_m2p}
 
 
-def run_reference(args, world, rank):
+def run_reference(args, world, rank, workload=None):
     if rank != 0:
         return
     from workloads import config_large
-    pr = config_large()
+    pr = workload() if workload is not None else config_large()
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle_baseline(pr, 2048, 1 << 16, threads)

@@ -710,6 +710,10 @@ int or_p2m(int n, int64_t N, const double *pos, int C, const double *vals, int s
     Geo g = make_geo(n, N, pos, cs, perm, qs);
     int64_t nn = (int64_t)n * n;
     if (node_end < 0 || node_end > nn) node_end = nn;
+    if (node_begin < 0 || node_begin > node_end) {
+        free(cs); free(perm); free(qs);
+        return OR_ERR_ARG;
+    }
     int err = OR_OK;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
     {
@@ -960,6 +964,10 @@ int or_p2m_backward(int n, int64_t N, const double *pos, int C, const double *va
     for (int64_t i = 0; i < N * 2; ++i) grad_pos[i] = 0;
     int64_t nn = (int64_t)n * n;
     if (node_end < 0 || node_end > nn) node_end = nn;
+    if (node_begin < 0 || node_begin > node_end) {
+        free(cs); free(perm); free(qs);
+        return OR_ERR_ARG;
+    }
     NodeQ Q;
     memset(&Q, 0, sizeof(Q));
     WSet s;

@@ -368,3 +368,10 @@ def test_m2p_adjoint(small):
             pm[m, dim] -= step
             fd = ((O.m2p(n, pp, f) - O.m2p(n, pm, f)) * gv).sum() / (2 * step)
             assert abs(fd - gp[m, dim]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_node_range_is_validated():
+    pos = G.jittered_lattice(16, 0.25, 5)
+    with pytest.raises(O.OracleError) as e:
+        O.p2m(9, pos, np.ones((pos.shape[0], 1)), shape=1, node_range=(-5, 10))
+    assert e.value.code == 1
