@@ -348,6 +348,13 @@ def run_ours(args, world, rank, local):
         return a.elapsed_time(b) / reps
     side = {}
     side["p2m_linear_ms"] = timeit(lambda: proj.p2m(vals, shape=P.PFEM_SHAPE_LINEAR, out=mesh))
+    side["m2p_mesh_qcsf_ms"] = timeit(lambda: proj.m2p(pos, mesh, out=back, shape=P.PFEM_SHAPE_QUADRATIC))
+    def projfemq():     # quadratic both ways: the paper's projFEMq interpolation pair
+        proj.build(pos)
+        proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=solve, out=mesh)
+        proj.m2p(pos, mesh, out=back, shape=P.PFEM_SHAPE_QUADRATIC)
+    side["projfemq_round_trip_ms"] = timeit(projfemq)
+    side["projfemq_round_trip_mparticles_s"] = N / (side["projfemq_round_trip_ms"] * 1e-3) / 1e6
     for nm, sv in (("f64", P.PFEM_SOLVE_F64), ("f32ref", P.PFEM_SOLVE_F32_REFINED), ("f32", P.PFEM_SOLVE_F32)):
         side[f"p2m_quadratic_solve_{nm}_ms"] = timeit(
             lambda: proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv, out=mesh))

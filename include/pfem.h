@@ -176,6 +176,18 @@ pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype po
  * and a transposed index over the N particles. */
 size_t pfem_backward_workspace_size(int32_t n, int64_t N, int32_t K);
 
+/* M2P (Sec. 2.2 eq. m2p) with quadratically consistent MESH shape functions (App. B applied
+ * to the fixed mesh; Table 1's projFEM6/projFEMq interpolate mesh -> particles with them):
+ * w_i = lambda_i [i in T] + sum over T's edges (P,Q) of 2 lambda_P lambda_Q A_{i,(P,Q)}, where
+ * each mesh edge's stencil is the closed neighbourhood of its endpoints (10 nodes of the
+ * (i,j)->(i+1,j+1)-split mesh) and A is the minimum-norm solution of eqs. A0, A1, condquad;
+ * on the uniform mesh A depends only on the edge direction and is computed once.  Values
+ * are read at the unique nodes (I mod (n-1), J mod (n-1)).  FP64 (FP64 positions), FP32 or
+ * BF16 storage (FP32 positions).  No workspace, no device errors. */
+pfem_status pfem_interp_m2p_quadratic(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
+                                      int32_t C, const void *mesh_vals, void *vals,
+                                      pfem_dtype val_t, void *stream);
+
 /* Adjoint of P2M with respect to particle values and positions, for an upstream gradient
  * grad_mesh [n, n, C] (each stored entry, image copies included, is its own output):
  *   grad_vals [N, C] out (original order when perm != NULL, slot order otherwise)

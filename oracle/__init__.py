@@ -13,6 +13,8 @@ from .oracle import (  # noqa: F401
     star,
     p2m,
     m2p,
+    m2p_quadratic,
+    mesh_edge,
     p2m_backward,
     m2p_backward,
     fixed_point,

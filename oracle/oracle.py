@@ -62,6 +62,8 @@ def lib():
         L.or_p2m_backward.argtypes = [i32, i64, _f64p, i32, _f64p, i32, _f64p, _f64p, _f64p,
                                       i64, i64]
         L.or_m2p_backward.argtypes = [i32, i64, _f64p, i32, _f64p, _f64p, _f64p, _f64p]
+        L.or_m2p_quadratic.argtypes = [i32, i64, _f64p, i32, _f64p, _f64p]
+        L.or_mesh_edge.argtypes = [i32, _i32p, _f64p]
         _lib = L
     return _lib
 
@@ -160,6 +162,27 @@ def p2m(n: int, pos, vals, shape: int = 1, nthreads: int = 1,
     b, e = node_range if node_range is not None else (0, -1)
     _check(lib().or_p2m(n, pos.shape[0], pos, C, vals, shape, mesh, nthreads, b, e), "p2m")
     return mesh.reshape(n, n, C)
+
+
+def mesh_edge(edge_type: int):
+    """(node offsets [k,2] from the edge's first node, coefficients A [k]) of a mesh edge of
+    direction (1,0), (0,1) or (1,1) (edge_type 0, 1, 2)."""
+    off = np.zeros(32, np.int32)
+    A = np.zeros(16)
+    k = lib().or_mesh_edge(edge_type, off, A)
+    if k < 0:
+        raise OracleError(1, "mesh_edge")
+    return off[: 2 * k].reshape(k, 2).copy(), A[:k].copy()
+
+
+def m2p_quadratic(n: int, pos, mesh) -> np.ndarray:
+    """M2P with quadratically consistent mesh shape functions -> [N, C]."""
+    pos = _pos(pos)
+    mesh = np.ascontiguousarray(np.asarray(mesh, dtype=np.float64).reshape(n * n, -1))
+    C = mesh.shape[1]
+    vals = np.zeros((pos.shape[0], C))
+    _check(lib().or_m2p_quadratic(n, pos.shape[0], pos, C, mesh, vals), "m2p_quadratic")
+    return vals
 
 
 def m2p(n: int, pos, mesh) -> np.ndarray:

@@ -806,6 +806,105 @@ int or_m2p_backward(int n, int64_t N, const double *pos, int C, const double *me
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ mesh QCSF (M2P)
+ *
+ * Quadratically consistent shape functions on the fixed mesh (App. B applied to the mesh
+ * triangulation; the paper's projFEM6 and projFEMq interpolate mesh -> particles with them,
+ * Table 1, and compute their geometric coefficients once, Sec. 3.1).  Every cell is split
+ * along (i,j)->(i+1,j+1), so node (I,J) has the six neighbours (I+-1,J), (I,J+-1), (I+1,J+1),
+ * (I-1,J-1).  An edge's stencil is the closed neighbourhood of both endpoints (10 nodes) and
+ * its coefficients are the minimum-norm solution of eqs. A0, A1, condquad; on the uniform
+ * mesh they depend only on the edge's direction: (1,0), (0,1) or (1,1). */
+
+static const int MESH_NB[6][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, -1}};
+
+/* Stencil (node offsets from the edge's first node) and coefficients of the mesh edge from
+ * (0,0) to (ex,ey). */
+static int mesh_edge(int ex, int ey, int S[16][2], double A[16])
+{
+    int k = 0;
+    int ends[2][2] = {{0, 0}, {ex, ey}};
+    for (int e = 0; e < 2; ++e)
+        for (int m = -1; m < 6; ++m) {
+            int x = ends[e][0] + (m < 0 ? 0 : MESH_NB[m][0]);
+            int y = ends[e][1] + (m < 0 ? 0 : MESH_NB[m][1]);
+            int dup = 0;
+            for (int i = 0; i < k; ++i)
+                if (S[i][0] == x && S[i][1] == y) dup = 1;
+            if (!dup) { S[k][0] = x; S[k][1] = y; ++k; }
+        }
+    double s = sqrt((double)(ex * ex + ey * ey));
+    double pk[OR_KSTEN][6];
+    for (int i = 0; i < k; ++i) {
+        double x = (S[i][0] - 0.5 * ex) / s, y = (S[i][1] - 0.5 * ey) / s;
+        pk[i][0] = 1; pk[i][1] = x; pk[i][2] = y; pk[i][3] = x * x; pk[i][4] = x * y; pk[i][5] = y * y;
+    }
+    double tx = ex / s, ty = ey / s;
+    double b[6] = {0, 0, 0, -0.5 * tx * tx, -0.5 * tx * ty, -0.5 * ty * ty};
+    minnorm_svd(k, pk, b, A);
+    return k;
+}
+
+/* Stencil and coefficients of a mesh edge type: 0 = (1,0), 1 = (0,1), 2 = (1,1). */
+int or_mesh_edge(int type, int32_t *offsets /*[16][2]*/, double *A /*[16]*/)
+{
+    static const int D[3][2] = {{1, 0}, {0, 1}, {1, 1}};
+    if (type < 0 || type > 2) return -1;
+    int S[16][2];
+    int k = mesh_edge(D[type][0], D[type][1], S, A);
+    for (int i = 0; i < k; ++i) { offsets[2 * i] = S[i][0]; offsets[2 * i + 1] = S[i][1]; }
+    return k;
+}
+
+/* M2P with mesh QCSF: alpha_mu = sum_i w_i alpha_i, w_i = lambda_i [i in T] +
+ * sum over the edges (P, Q) of T of 2 lambda_P lambda_Q A_{i,(P,Q)} (eq. phiquad on the mesh).
+ * Node values are read at unique nodes (I mod (n-1), J mod (n-1)). */
+int or_m2p_quadratic(int n, int64_t N, const double *pos, int C, const double *mesh, double *vals)
+{
+    if (n < 3 || N < 0 || C < 1) return OR_ERR_ARG;
+    int nc = n - 1;
+    int S[3][16][2];
+    double A[3][16];
+    int K[3];
+    static const int D[3][2] = {{1, 0}, {0, 1}, {1, 1}};
+    for (int t = 0; t < 3; ++t) K[t] = mesh_edge(D[t][0], D[t][1], S[t], A[t]);
+    for (int64_t m = 0; m < N; ++m) {
+        double x = pos[2 * m], y = pos[2 * m + 1];
+        int i = cell_of(fx_of(x), nc), j = cell_of(fx_of(y), nc);
+        double s = wrap_unit(x - (double)i / nc) * nc;
+        double t = wrap_unit(y - (double)j / nc) * nc;
+        int V[3][2];
+        double lam[3];
+        if (s >= t) {
+            V[0][0] = 0; V[0][1] = 0; V[1][0] = 1; V[1][1] = 0; V[2][0] = 1; V[2][1] = 1;
+            lam[0] = 1 - s; lam[1] = s - t; lam[2] = t;
+        } else {
+            V[0][0] = 0; V[0][1] = 0; V[1][0] = 1; V[1][1] = 1; V[2][0] = 0; V[2][1] = 1;
+            lam[0] = 1 - t; lam[1] = s; lam[2] = t - s;
+        }
+        for (int c = 0; c < C; ++c) vals[m * C + c] = 0;
+        for (int e = 0; e < 3; ++e) {
+            int I = ((i + V[e][0]) % nc + nc) % nc, J = ((j + V[e][1]) % nc + nc) % nc;
+            for (int c = 0; c < C; ++c) vals[m * C + c] += lam[e] * mesh[((int64_t)J * n + I) * C + c];
+        }
+        for (int e = 0; e < 3; ++e) {
+            int f = (e + 1) % 3;
+            int dx = V[f][0] - V[e][0], dy = V[f][1] - V[e][1];
+            int bx = V[e][0], by = V[e][1];
+            if (dx < 0 || dy < 0) { dx = -dx; dy = -dy; bx = V[f][0]; by = V[f][1]; }
+            int type = (dx == 1 && dy == 0) ? 0 : (dx == 0 && dy == 1) ? 1 : 2;
+            double cf = 2.0 * lam[e] * lam[f];
+            for (int k = 0; k < K[type]; ++k) {
+                int I = ((i + bx + S[type][k][0]) % nc + nc) % nc;
+                int J = ((j + by + S[type][k][1]) % nc + nc) % nc;
+                for (int c = 0; c < C; ++c)
+                    vals[m * C + c] += cf * A[type][k] * mesh[((int64_t)J * n + I) * C + c];
+            }
+        }
+    }
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ complex step */
 
 typedef double _Complex cplx;

@@ -45,6 +45,8 @@ SIGNATURES = {
                                         ctypes.c_int, _p, _p, _sz, _p]),
     "pfem_interp_m2p": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int, _p]),
     "pfem_backward_workspace_size": (_sz, [_i32, _i64, _i32]),
+    "pfem_interp_m2p_quadratic": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _i32, _p, _p,
+                                                 ctypes.c_int, _p]),
     "pfem_project_backward": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _i32,
                                              _p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, _p, _p, _i32, ctypes.c_int, _p, _p, _p,

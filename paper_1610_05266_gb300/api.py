@@ -93,6 +93,12 @@ def pfem_backward_workspace_size(n: int, N: int, K: int) -> int:
     return int(L.load().pfem_backward_workspace_size(n, N, K))
 
 
+def pfem_interp_m2p_quadratic(n, N, pos, C, mesh_vals, vals, stream=None):
+    check(L.load().pfem_interp_m2p_quadratic(n, N, ptr(pos), dtype_code(pos.dtype), C,
+                                             ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype),
+                                             stream_ptr(stream)), "pfem_interp_m2p_quadratic")
+
+
 def pfem_project_backward(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape,
                           solve, mode, w_idx, w, K, grad_mesh, grad_vals, grad_pos, ws,
                           stream=None):
@@ -233,11 +239,16 @@ class Projector:
         pfem_delaunay_stars(self.nb, self.N, c.q_sorted, c.cell_start, nbrs, counts, c.ws, stream)
         return nbrs, counts
 
-    def m2p(self, pos: torch.Tensor, mesh: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    def m2p(self, pos: torch.Tensor, mesh: torch.Tensor, out=None, shape=PFEM_SHAPE_LINEAR,
+            stream=None) -> torch.Tensor:
+        """M2P with linear FE (default) or quadratically consistent mesh shape functions."""
         C = mesh.shape[-1]
         if out is None:
             out = torch.empty((pos.shape[0], C), dtype=mesh.dtype, device=mesh.device)
-        pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream)
+        if shape == PFEM_SHAPE_QUADRATIC:
+            pfem_interp_m2p_quadratic(self.n, pos.shape[0], pos, C, mesh, out, stream)
+        else:
+            pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream)
         return out
 
     def backward(self, vals: torch.Tensor, grad_mesh: torch.Tensor, shape=PFEM_SHAPE_QUADRATIC,

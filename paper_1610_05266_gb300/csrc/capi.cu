@@ -240,6 +240,18 @@ size_t pfem_backward_workspace_size(int32_t n, int64_t N, int32_t K)
     return bwd_layout(n, N, K).total;
 }
 
+pfem_status pfem_interp_m2p_quadratic(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
+                                      int32_t C, const void *mesh_vals, void *vals,
+                                      pfem_dtype val_t, void *stream)
+{
+    if (n < 9 || N < 0 || N >= (1LL << 40) || C < 1 || C > 8) return PFEM_ERR_INVALID_ARG;
+    if (N > 0 && (!pos || !mesh_vals || !vals)) return PFEM_ERR_INVALID_ARG;
+    if (!((val_t == PFEM_F64 && pos_t == PFEM_F64) || (val_t != PFEM_F64 && pos_t == PFEM_F32)))
+        return PFEM_ERR_INVALID_ARG;
+    return from_cuda(launch_m2p_quadratic(n, N, pos, pos_t, C, mesh_vals, vals, val_t,
+                                          (cudaStream_t)stream));
+}
+
 pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                   pfem_dtype pos_t, const uint32_t *q_sorted,
                                   const int32_t *cell_start, const int32_t *perm, int32_t C,

@@ -232,3 +232,34 @@ def test_tiled_and_per_thread_paths_agree(P, dtype, shape, monkeypatch):
         plain = proj.p2m(v, shape=shape)
         proj.check()
         assert torch.equal(tiled, plain), (n, M)
+
+
+def test_m2p_mesh_qcsf_matches_oracle(P):
+    """M2P with quadratically consistent mesh shape functions (the paper's projFEM6/projFEMq
+    interpolation): FP64 within 1e-12 of the oracle on ragged sizes; reduced-precision errors
+    stated."""
+    for n, M in ((33, 64), (26, 50), (129, 256)):
+        pos = G.jittered_lattice(M, 0.3, G.SEED_BASE + 200 + n)
+        mesh = np.random.default_rng(n).standard_normal((n, n, 3))
+        proj = P.Projector(n, pos.shape[0], pos_dtype=torch.float64)
+        out = proj.m2p(torch.tensor(pos, device="cuda"), torch.tensor(mesh, device="cuda"),
+                       shape=P.PFEM_SHAPE_QUADRATIC)
+        ref = O.m2p_quadratic(n, pos, mesh)
+        assert relerr(out.cpu().numpy(), ref) <= TOL64, n
+    pos32 = torch.tensor(pos, dtype=torch.float32, device="cuda")
+    ref32 = O.m2p_quadratic(n, pos.astype(np.float32).astype(np.float64), mesh)
+    e32 = relerr(proj.m2p(pos32, torch.tensor(mesh, dtype=torch.float32, device="cuda"),
+                          shape=P.PFEM_SHAPE_QUADRATIC).cpu().numpy(), ref32)
+    print(f"mesh-QCSF M2P error vs FP64 oracle: fp32 {e32:.2e}")
+    assert e32 < 1e-5
+
+
+def test_projfemq_round_trip(P):
+    """projFEMq round trip (particle QCSF P2M, then mesh QCSF M2P) against the oracle."""
+    pr = G.config_tiny()
+    proj, pos = gpu_setup(P, pr)
+    mesh = proj.p2m(torch.tensor(pr.vals, device="cuda"), shape=P.PFEM_SHAPE_QUADRATIC)
+    back = proj.m2p(pos, mesh, shape=P.PFEM_SHAPE_QUADRATIC)
+    ref_mesh = O.p2m(pr.n, pr.pos, pr.vals, shape=1, nthreads=8)
+    ref = O.m2p_quadratic(pr.n, pr.pos, ref_mesh)
+    assert relerr(back.cpu().numpy(), ref) <= TOL64

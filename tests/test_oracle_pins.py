@@ -375,3 +375,68 @@ def test_node_range_is_validated():
     with pytest.raises(O.OracleError) as e:
         O.p2m(9, pos, np.ones((pos.shape[0], 1)), shape=1, node_range=(-5, 10))
     assert e.value.code == 1
+
+
+# ------------------------------------------------------------------ mesh QCSF (M2P)
+
+
+def test_mesh_edge_coefficients():
+    """Mesh-edge coefficients satisfy eqs. A0, A1, condquad on their 10-node stencils and are
+    the minimum-norm solution (LAPACK pseudo-inverse)."""
+    for t, d in enumerate(((1, 0), (0, 1), (1, 1))):
+        off, A = O.mesh_edge(t)
+        assert len(off) == 10 and len({tuple(o) for o in off}) == 10
+        d = np.array(d, float)
+        x = off.astype(float)
+        assert abs(A.sum()) < 1e-13 and np.abs(A @ x).max() < 1e-13
+        rhs = 0.5 * (-np.outer(d, d))          # nodes (0,0) and d: eq. condquad
+        lhs = np.einsum("k,ki,kj->ij", A, x, x)
+        assert np.abs(lhs - rhs).max() < 1e-13
+        P = np.stack([np.ones(10), x[:, 0], x[:, 1], x[:, 0] ** 2, x[:, 0] * x[:, 1], x[:, 1] ** 2])
+        b = np.array([0, 0, 0, rhs[0, 0], rhs[0, 1], rhs[1, 1]])
+        assert np.abs(A - np.linalg.pinv(P) @ b).max() < 1e-12
+
+
+def test_mesh_qcsf_m2p_reproduces_quadratics():
+    """Mesh QCSF reproduce quadratic fields exactly (eq. C2), where linear FE do not; checked
+    away from the periodic seam with a non-periodic quadratic in node coordinates."""
+    n = 33
+    nc = n - 1
+    II, JJ = np.meshgrid(np.arange(n), np.arange(n))
+    quad = lambda X, Y: 0.7 + 0.3 * X - 0.2 * Y + 0.05 * X * X - 0.03 * X * Y + 0.02 * Y * Y
+    mesh = quad(II.astype(float), JJ.astype(float))[..., None]
+    rng = np.random.default_rng(0)
+    pos = rng.uniform(3.0 / nc, (nc - 4.0) / nc, size=(500, 2))
+    exact = quad(pos[:, 0] * nc, pos[:, 1] * nc)
+    q = O.m2p_quadratic(n, pos, mesh)[:, 0]
+    l = O.m2p(n, pos, mesh)[:, 0]
+    assert np.abs(q - exact).max() < 1e-12 * np.abs(exact).max()
+    assert np.abs(l - exact).max() > 1e-4
+    # constants and linear fields everywhere (partition of unity, linear precision)
+    ones = np.ones((n, n, 1))
+    assert np.abs(O.m2p_quadratic(n, pos, ones) - 1).max() < 1e-13
+
+
+def test_mesh_qcsf_m2p_order_and_interpolation():
+    """M2P error on Taylor-Green fields falls as H^3 with mesh QCSF (H^2 with linear FE), and
+    a particle on a node takes the node's value."""
+    errs_q, errs_l, hs = [], [], []
+    for nc in (16, 32, 64, 128):
+        n = nc + 1
+        pos = G.jittered_lattice(2 * nc, 0.25, G.SEED_BASE + 80 + nc)
+        nodes = np.stack(np.meshgrid(np.arange(n) / nc, np.arange(n) / nc), -1).reshape(-1, 2)
+        mesh = G.taylor_green(nodes).reshape(n, n, 3)
+        exact = G.taylor_green(pos)
+        rel = lambda v: np.sqrt(((v - exact) ** 2).sum() / (exact ** 2).sum())
+        errs_q.append(rel(O.m2p_quadratic(n, pos, mesh)))
+        errs_l.append(rel(O.m2p(n, pos, mesh)))
+        hs.append(1.0 / nc)
+    sq = np.polyfit(np.log(hs), np.log(errs_q), 1)[0]
+    sl = np.polyfit(np.log(hs), np.log(errs_l), 1)[0]
+    assert abs(sl - 2) < 0.3 and abs(sq - 3) < 0.35, (sl, sq)
+    n = 17
+    mesh = np.random.default_rng(2).standard_normal((n, n, 2))
+    mesh[-1] = mesh[0]
+    mesh[:, -1] = mesh[:, 0]
+    p = np.array([[5 / 16, 9 / 16]])
+    assert np.abs(O.m2p_quadratic(n, p, mesh)[0] - mesh[9, 5]).max() < 1e-14
