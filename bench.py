@@ -374,6 +374,40 @@ def run_ours(args, world, rank, local):
     proj64.check("fp64 round trip")
     out["side"] = side
 
+    # --- differentiation workload: L = 1/2 sum_i (P2M_i - t_i)^2, backward to values and
+    #     positions, recompute vs checkpoint of the shape-function weights
+    if not args.no_grad:
+        from workloads import config_grad
+        gp_ = config_grad()
+        gpos = torch.tensor(gp_.pos, dtype=torch.float32, device=dev)
+        gvals = torch.tensor(gp_.vals, dtype=torch.float32, device=dev)
+        gtarget = torch.tensor(gp_.target, dtype=torch.float32, device=dev)
+        gproj = P.Projector(gp_.n, gp_.N, C=1, pos_dtype=torch.float32, device=dev)
+        gproj.build(gpos)
+        def fwd():
+            return gproj.p2m(gvals, shape=P.PFEM_SHAPE_QUADRATIC)
+        gmesh = fwd()
+        gbar = (gmesh - gtarget).contiguous()
+        t_fwd = timeit(fwd)
+        t_bwd_rec = timeit(lambda: gproj.backward(gvals, gbar))
+        wts = gproj.shape_weights(K=32, w_dtype=torch.float32)
+        t_shape = timeit(lambda: gproj.shape_weights(K=32, w_dtype=torch.float32))
+        t_fwd_ck = timeit(lambda: gproj.p2m(gvals, weights=wts))
+        t_bwd_ck = timeit(lambda: gproj.backward(gvals, gbar, weights=wts))
+        t_bwd_ck_vals = timeit(lambda: gproj.backward(gvals, gbar, weights=wts, want_pos=False))
+        code, _ = gproj.backward_status()
+        out["gradient"] = {"workload": gp_.name, "dtype": "f32", "status": code,
+                           "forward_fused_ms": t_fwd,
+                           "backward_recompute_ms": t_bwd_rec,
+                           "checkpoint_weights_ms": t_shape,
+                           "forward_from_checkpoint_ms": t_fwd_ck,
+                           "backward_checkpoint_ms": t_bwd_ck,
+                           "backward_checkpoint_values_only_ms": t_bwd_ck_vals,
+                           "step_recompute_ms": t_fwd + t_bwd_rec,
+                           "step_checkpoint_ms": t_shape + t_fwd_ck + t_bwd_ck}
+        del gproj, wts
+        torch.cuda.empty_cache()
+
     # --- batched uneven problems (256, persistent launches, tuned, CUDA graph) vs the plain
     #     FP64 single-instance form, problem by problem
     if not args.no_batched:
@@ -504,6 +538,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()

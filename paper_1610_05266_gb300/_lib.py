@@ -84,11 +84,12 @@ _lib = None
 
 
 def load(path: Optional[str] = None):
-    """Load libpfem.so (built by build.py); raises LibraryMissing if it is absent."""
+    """Load libpfem.so (built by build.py; PFEM_LIB selects another build of it); raises
+    LibraryMissing if it is absent."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("PFEM_LIB") or LIB_PATH
     if not os.path.exists(p):
         raise LibraryMissing(f"{p} is missing: build it with paper_1610_05266_gb300.build.build()")
     L = ctypes.CDLL(p)

@@ -35,14 +35,23 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False,
+          extra_flags=None, lib_path: str = None, build_dir: str = None) -> str:
+    """Compile every translation unit and link libpfem.so.  `extra_flags` (or the
+    PFEM_NVCC_FLAGS environment variable, space separated) are appended to the nvcc flags;
+    `lib_path`/`build_dir` redirect the outputs (used to build tuning variants side by side)."""
+    global BUILD, LIB
+    out_lib, out_dir = lib_path or LIB, build_dir or BUILD
+    extra_flags = list(extra_flags or []) + os.environ.get("PFEM_NVCC_FLAGS", "").split()
+    if extra_flags and build_dir is None:
+        out_dir = BUILD + "_" + "_".join(f.strip("-").replace("=", "") for f in extra_flags)
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     dep_t = _deps_mtime()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + extra_flags
 
     def compile_one(src: str):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         if (not force and not ptxas_info and os.path.exists(obj)
                 and os.path.getmtime(obj) > max(os.path.getmtime(src), dep_t)):
             return obj, ""
@@ -59,14 +68,14 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 print(log)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(out_lib) or os.path.getmtime(out_lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = out_lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, out_lib)
+    return out_lib
 
 
 if __name__ == "__main__":

@@ -232,7 +232,7 @@ __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
 }
 
 template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
-__global__ void __launch_bounds__(128) k_bwd_node(BwdArgs b)
+__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_bwd_node(BwdArgs b)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_bin_batch(const BPlanDev *pl, const P *
 // ---------------------------------------------------------------- P2M
 
 template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE>
-__global__ void k_p2m_batch(const BPlanDev *pl, int shape_idx, P2MArgs base,
+__global__ void __launch_bounds__(256, PFEM_P2M_MIN_BLOCKS / 2) k_p2m_batch(const BPlanDev *pl, int shape_idx, P2MArgs base,
                             unsigned long long *counter)
 {
     __shared__ long long item;

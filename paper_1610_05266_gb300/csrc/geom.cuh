@@ -227,7 +227,10 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
 // circumcircle lies inside the searched region and within distance D of v, so no particle
 // left out of the list can be inside it.
 
-constexpr int KL = 28;   // list capacity (about 20 particles lie within the cutoff)
+#ifndef PFEM_STAR_LIST
+#define PFEM_STAR_LIST 24
+#endif
+constexpr int KL = PFEM_STAR_LIST;   // list capacity (jittered lattices: at most 21 within the cutoff)
 
 struct FCirc {
     float K, P, Q, Ka, Pa, Qa;

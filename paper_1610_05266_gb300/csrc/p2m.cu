@@ -153,7 +153,7 @@ cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_d
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(128) k_stars(Bins B, int R0, long long N, int *nbrs, int *counts,
+__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_stars(Bins B, int R0, long long N, int *nbrs, int *counts,
                                                DevStatus *st)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;

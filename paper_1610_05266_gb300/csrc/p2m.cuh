@@ -427,8 +427,15 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
     }
 }
 
+// Resident blocks per SM the compiler must allow (it caps registers at 65536 / (128 x 12) = 42):
+// the per-node work is latency-bound, and measured on GB300 (sweep 1..16) twelve 128-thread
+// blocks per SM were fastest despite the extra register spills.
+#ifndef PFEM_P2M_MIN_BLOCKS
+#define PFEM_P2M_MIN_BLOCKS 12
+#endif
+
 template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS>
-__global__ void __launch_bounds__(128) k_p2m(P2MArgs a)
+__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m(P2MArgs a)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
