@@ -31,22 +31,6 @@ struct BwdArgs {
 
 constexpr int KBWD = 32;   // distinct particles per node kept by the recompute kernel
 
-template <typename R> struct Entry {
-    int slot;
-    R w, dx, dy;
-};
-
-template <typename R>
-__device__ __forceinline__ int entry_of(Entry<R> *E, int &cnt, int K, int s, bool &over)
-{
-    for (int i = 0; i < cnt; ++i)
-        if (E[i].slot == s) return i;
-    if (cnt == K) { over = true; return -1; }
-    E[cnt].slot = s;
-    E[cnt].w = E[cnt].dx = E[cnt].dy = R(0);
-    return cnt++;
-}
-
 template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
 __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
 {
@@ -65,9 +49,10 @@ __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
         g[c] = c < a.C ? load_val<V, R>((const V *)b.grad_mesh + node * a.C + c) : R(0);
         any |= g[c] != R(0);
     }
-    Entry<R> E[KBWD];
-    int cnt = 0;
-    bool over = false;
+    // the node's distinct particles U: slot, weight, beta = gbar . alpha, position adjoint
+    int us[UMAX];
+    R uw[UMAX], ub[UMAX], udx[UMAX], udy[UMAX];
+    int nu = 0;
     int st = 0;
     if (any) {
         const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
@@ -85,148 +70,158 @@ __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
         if (st == 0) {
             NodePos<P, R> np;
             np.init(Iu, Ju, nc);
-            R d[3][2];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
-            const R Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
-            const R Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
-            const R Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
-            const R A2 = Na + Nb + Nc;
-            const R lam[3] = {Na / A2, Nb / A2, Nc / A2};
-            R lbar[3] = {R(0), R(0), R(0)};
-            auto beta_of = [&](int s) {
-                R v[8];
-                load_vals<V, R>((const V *)a.vals, a.perm, s, a.C, v);
-                R t = R(0);
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (c < a.C) t = fma(g[c], v[c], t);
-                return t;
+            bool over = false;
+            auto add = [&](int s) -> int {
+                for (int i = 0; i < nu; ++i)
+                    if (us[i] == s) return i;
+                if (nu == UMAX || nu == b.K) { over = true; return 0; }
+                us[nu] = s;
+                uw[nu] = udx[nu] = udy[nu] = R(0);
+                return nu++;
             };
-            int ti[3];
+            int vi[3];
+            unsigned vm[3] = {0u, 0u, 0u};
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                ti[e] = entry_of(E, cnt, b.K, tri[e], over);
-                if (ti[e] >= 0) E[ti[e]].w += lam[e];
-                lbar[e] += beta_of(tri[e]);
-            }
-            if (SHAPE == PFEM_SHAPE_QUADRATIC) {
-                for (int e = 0; e < 3 && st == 0 && !over; ++e) {
-                    const int f = e == 2 ? 0 : e + 1;
-                    const int nu = tri[e], sg = tri[f];
-                    const int *st_nu = stars[e], *st_sg = stars[f];
-                    const int n_nu = ns[e], n_sg = ns[f];
-                    const S rnx = S(d[e][0]), rny = S(d[e][1]), rsx = S(d[f][0]), rsy = S(d[f][1]);
-                    const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
-                    const S ex = rnx - rsx, ey = rny - rsy;
-                    const S inv = S(1) / sqrt(ex * ex + ey * ey);
-                    auto for_stencil = [&](auto &&fn) {
-                        fn(nu);
-                        for (int i = 0; i < n_nu; ++i) fn(st_nu[i]);
-                        for (int j = 0; j < n_sg; ++j) {
-                            const int m = st_sg[j];
-                            if (m == nu || in_list(st_nu, n_nu, m)) continue;
-                            fn(m);
+            for (int e = 0; e < 3; ++e) vi[e] = add(tri[e]);
+            if (SHAPE == PFEM_SHAPE_QUADRATIC)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    unsigned m = 1u << vi[e];
+                    for (int i = 0; i < ns[e]; ++i) m |= 1u << add(stars[e][i]);
+                    vm[e] = m;
+                }
+            if (over) st = -PFEM_ERR_CAPACITY;
+            if (st == 0) {
+                for (int i = 0; i < nu; ++i) {
+                    R v[8];
+                    load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
+                    R t = R(0);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < a.C) t = fma(g[c], v[c], t);
+                    ub[i] = t;
+                }
+                R d[3][2];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
+                const R Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
+                const R Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
+                const R Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
+                const R A2 = Na + Nb + Nc;
+                const R lam[3] = {Na / A2, Nb / A2, Nc / A2};
+                R lbar[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    uw[vi[e]] += lam[e];
+                    lbar[e] = ub[vi[e]];
+                }
+                auto offset = [&](int i, S &x, S &y) {
+                    R dx, dy;
+                    np.off(a.pos, us[i], dx, dy);
+                    x = S(dx);
+                    y = S(dy);
+                };
+                if (SHAPE == PFEM_SHAPE_QUADRATIC)
+                    for (int e = 0; e < 3 && st == 0; ++e) {
+                        const int f = e == 2 ? 0 : e + 1;
+                        const unsigned mask = vm[e] | vm[f];
+                        const S rnx = S(d[e][0]), rny = S(d[e][1]), rsx = S(d[f][0]), rsy = S(d[f][1]);
+                        const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
+                        const S ex = rnx - rsx, ey = rny - rsy;
+                        const S inv = S(1) / sqrt(ex * ex + ey * ey);
+                        Moment<S> M;
+                        M.zero();
+                        S u[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+                        for (unsigned m = mask; m; m &= m - 1) {
+                            const int i = __ffs(m) - 1;
+                            S ox, oy;
+                            offset(i, ox, oy);
+                            const S x = (ox - mx) * inv, y = (oy - my) * inv;
+                            M.add(x, y);
+                            const S bt = S(ub[i]);
+                            const S p[6] = {S(1), x, y, x * x, x * y, y * y};
+#pragma unroll
+                            for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
                         }
-                    };
-                    auto coords = [&](int s, S &x, S &y) {
-                        R dx, dy;
-                        np.off(a.pos, s, dx, dy);
-                        x = (S(dx) - mx) * inv;
-                        y = (S(dy) - my) * inv;
-                    };
-                    Moment<S> M;
-                    M.zero();
-                    S u[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-                    for_stencil([&](int s) {
-                        S x, y;
-                        coords(s, x, y);
-                        M.add(x, y);
-                        const S bt = S(beta_of(s));
-                        const S p[6] = {S(1), x, y, x * x, x * y, y * y};
+                        if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
+                        const S tx = ex * inv, ty = ey * inv;
+                        const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
+                                         S(-0.5) * ty * ty};
+                        S y[6], z[6];
+                        M.solve(bb, y);
+                        M.solve(u, z);
+                        const S ce = S(2) * S(lam[e]) * S(lam[f]);
+                        S Be = S(0);
 #pragma unroll
-                        for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
-                    });
-                    if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
-                    const S tx = ex * inv, ty = ey * inv;
-                    const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
-                                     S(-0.5) * ty * ty};
-                    S y[6], z[6];
-                    M.solve(bb, y);
-                    M.solve(u, z);
-                    const S ce = S(2) * S(lam[e]) * S(lam[f]);
-                    S Be = S(0);
+                        for (int r = 0; r < 6; ++r) Be = fma(u[r], y[r], Be);
+                        lbar[e] += R(S(2) * S(lam[f]) * Be);
+                        lbar[f] += R(S(2) * S(lam[e]) * Be);
+                        for (unsigned m = mask; m; m &= m - 1) {
+                            const int i = __ffs(m) - 1;
+                            S ox, oy;
+                            offset(i, ox, oy);
+                            const S x = (ox - mx) * inv, yy = (oy - my) * inv;
+                            const S p[6] = {S(1), x, yy, x * x, x * yy, yy * yy};
+                            S Am = S(0), Zm = S(0);
 #pragma unroll
-                    for (int r = 0; r < 6; ++r) Be = fma(u[r], y[r], Be);
-                    lbar[e] += R(S(2) * S(lam[f]) * Be);
-                    lbar[f] += R(S(2) * S(lam[e]) * Be);
-                    for_stencil([&](int s) {
-                        S x, yy;
-                        coords(s, x, yy);
-                        const S p[6] = {S(1), x, yy, x * x, x * yy, yy * yy};
-                        S Am = S(0), Zm = S(0);
+                            for (int r = 0; r < 6; ++r) {
+                                Am = fma(p[r], y[r], Am);
+                                Zm = fma(p[r], z[r], Zm);
+                            }
+                            uw[i] += R(ce * Am);
+                            if (POS) {
+                                const S bt = S(ub[i]);
+                                S pb[6];
 #pragma unroll
-                        for (int r = 0; r < 6; ++r) {
-                            Am = fma(p[r], y[r], Am);
-                            Zm = fma(p[r], z[r], Zm);
+                                for (int r = 0; r < 6; ++r) pb[r] = ce * ((bt - Zm) * y[r] - Am * z[r]);
+                                const S xb = pb[1] + S(2) * x * pb[3] + yy * pb[4];
+                                const S yb = pb[2] + x * pb[4] + S(2) * yy * pb[5];
+                                udx[i] += R(xb * inv);
+                                udy[i] += R(yb * inv);
+                            }
                         }
-                        const int k = entry_of(E, cnt, b.K, s, over);
-                        if (k < 0) return;
-                        E[k].w += R(ce * Am);
                         if (POS) {
-                            const S bt = S(beta_of(s));
-                            S pb[6];
-#pragma unroll
-                            for (int r = 0; r < 6; ++r) pb[r] = ce * ((bt - Zm) * y[r] - Am * z[r]);
-                            const S xb = pb[1] + S(2) * x * pb[3] + yy * pb[4];
-                            const S yb = pb[2] + x * pb[4] + S(2) * yy * pb[5];
-                            E[k].dx += R(xb * inv);
-                            E[k].dy += R(yb * inv);
+                            // b = [0,0,0,-tx^2/2,-tx ty/2,-ty^2/2], t = (r_nu - r_sg)/s
+                            const S txb = ce * (-tx * z[3] - S(0.5) * ty * z[4]);
+                            const S tyb = ce * (-S(0.5) * tx * z[4] - ty * z[5]);
+                            udx[vi[e]] += R(txb * inv);
+                            udy[vi[e]] += R(tyb * inv);
+                            udx[vi[f]] -= R(txb * inv);
+                            udy[vi[f]] -= R(tyb * inv);
                         }
-                    });
-                    if (POS && !over) {
-                        // b = [0,0,0,-tx^2/2,-tx ty/2,-ty^2/2], t = (r_nu - r_sg)/s
-                        const S txb = ce * (-tx * z[3] - S(0.5) * ty * z[4]);
-                        const S tyb = ce * (-S(0.5) * tx * z[4] - ty * z[5]);
-                        E[ti[e]].dx += R(txb * inv);
-                        E[ti[e]].dy += R(tyb * inv);
-                        E[ti[f]].dx -= R(txb * inv);
-                        E[ti[f]].dy -= R(tyb * inv);
+                    }
+                if (POS && st == 0) {
+                    // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
+                    const R Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
+                    const R nb0 = (lbar[0] - Lam) / A2, nb1 = (lbar[1] - Lam) / A2, nb2 = (lbar[2] - Lam) / A2;
+                    // cross(u, v): d/du = (v.y, -v.x), d/dv = (-u.y, u.x)
+                    R gx[3] = {R(0), R(0), R(0)}, gy[3] = {R(0), R(0), R(0)};
+                    gx[1] += nb0 * d[2][1];  gy[1] -= nb0 * d[2][0];
+                    gx[2] -= nb0 * d[1][1];  gy[2] += nb0 * d[1][0];
+                    gx[2] += nb1 * d[0][1];  gy[2] -= nb1 * d[0][0];
+                    gx[0] -= nb1 * d[2][1];  gy[0] += nb1 * d[2][0];
+                    gx[0] += nb2 * d[1][1];  gy[0] -= nb2 * d[1][0];
+                    gx[1] -= nb2 * d[0][1];  gy[1] += nb2 * d[0][0];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        udx[vi[e]] += gx[e];
+                        udy[vi[e]] += gy[e];
                     }
                 }
             }
-            if (POS && st == 0 && !over) {
-                // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
-                const R Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
-                const R nb0 = (lbar[0] - Lam) / A2, nb1 = (lbar[1] - Lam) / A2, nb2 = (lbar[2] - Lam) / A2;
-                // cross(u, v): d/du = (v.y, -v.x), d/dv = (-u.y, u.x)
-                R gx[3] = {R(0), R(0), R(0)}, gy[3] = {R(0), R(0), R(0)};
-                gx[1] += nb0 * d[2][1];  gy[1] -= nb0 * d[2][0];
-                gx[2] -= nb0 * d[1][1];  gy[2] += nb0 * d[1][0];
-                gx[2] += nb1 * d[0][1];  gy[2] -= nb1 * d[0][0];
-                gx[0] -= nb1 * d[2][1];  gy[0] += nb1 * d[2][0];
-                gx[0] += nb2 * d[1][1];  gy[0] -= nb2 * d[1][0];
-                gx[1] -= nb2 * d[0][1];  gy[1] += nb2 * d[0][0];
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    E[ti[e]].dx += gx[e];
-                    E[ti[e]].dy += gy[e];
-                }
-            }
         }
-        if (over && st == 0) st = -PFEM_ERR_CAPACITY;
         if (st != 0) {
             record_error(a.status, -st, node);
-            cnt = 0;
+            nu = 0;
         }
     }
     for (int k = 0; k < b.K; ++k) {
-        const bool v = k < cnt;
-        oslot[k] = v ? E[k].slot : -1;
-        ow[k] = v ? E[k].w : R(0);
+        const bool v = k < nu;
+        oslot[k] = v ? us[k] : -1;
+        ow[k] = v ? uw[k] : R(0);
         if (POS) {
-            od[2 * k] = v ? E[k].dx : R(0);
-            od[2 * k + 1] = v ? E[k].dy : R(0);
+            od[2 * k] = v ? udx[k] : R(0);
+            od[2 * k + 1] = v ? udy[k] : R(0);
         }
     }
 }
