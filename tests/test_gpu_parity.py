@@ -263,3 +263,31 @@ def test_projfemq_round_trip(P):
     ref_mesh = O.p2m(pr.n, pr.pos, pr.vals, shape=1, nthreads=8)
     ref = O.m2p_quadratic(pr.n, pr.pos, ref_mesh)
     assert relerr(back.cpu().numpy(), ref) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_six_particles_per_node(P, shape):
+    """The paper's fine density h = H/sqrt(6) (projFEM6 / projFEMq6 configurations)."""
+    pr = G.six_per_node(32)
+    proj, _ = gpu_setup(P, pr)
+    mesh = proj.p2m(torch.tensor(pr.vals, device="cuda"), shape=shape)
+    proj.check()
+    assert relerr(mesh.cpu().numpy(), O.p2m(pr.n, pr.pos, pr.vals, shape=shape, nthreads=8)) <= TOL64
+
+
+@pytest.mark.parametrize("a", [0.0, 0.2])
+def test_particles_recreated_at_nodes(P, a):
+    """Particles re-created at the nodes (Discussion): unjittered, every node coincides with a
+    particle and P2M returns the particle values exactly (interpolating shape functions);
+    jittered, values match the oracle."""
+    pr = G.particles_at_nodes(32, a=a)
+    proj, _ = gpu_setup(P, pr)
+    for shape in (0, 1):
+        mesh = proj.p2m(torch.tensor(pr.vals, device="cuda"), shape=shape).cpu().numpy()
+        proj.check()
+        ref = O.p2m(pr.n, pr.pos, pr.vals, shape=shape, nthreads=8)
+        assert relerr(mesh, ref) <= TOL64
+        if a == 0.0:
+            nc = pr.n - 1
+            vals = pr.vals.reshape(nc, nc, 3)
+            assert np.abs(mesh[:nc, :nc] - vals).max() <= 1e-15

@@ -25,4 +25,6 @@ from .generators import (  # noqa: F401
     config_batched,
     config_grad,
     scaled_config,
+    six_per_node,
+    particles_at_nodes,
 )

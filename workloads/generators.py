@@ -219,3 +219,28 @@ def scaled_config(which: str, n: int, M: int, a: float = 0.25, seed_offset: int 
         rho = rayleigh_taylor(pos, 1.0 / (n - 1))[:, None]
         return Problem(f"rt_{n}_{M}", n, M, a, seed, pos, rho, ["rho"])
     raise ValueError(which)
+
+
+def six_per_node(nc: int, a: float = 0.25, seed_offset: int = 0) -> Problem:
+    """The paper's 'fine' density of six particles per mesh node (h = H/sqrt(6), Sec. 3.1,
+    projFEM6 / projFEMq6): an M x M jittered lattice with M = round(sqrt(6) nc)."""
+    M = int(round(np.sqrt(6.0) * nc))
+    return _tg_problem(f"six_per_node_{nc + 1}_{M}", nc + 1, M, a, SEED_BASE + 40 + seed_offset)
+
+
+def particles_at_nodes(nc: int, a: float = 0.0, seed: int = SEED_BASE + 50) -> Problem:
+    """Particles re-created at the mesh nodes (Discussion, Eulerian-spirit variant): one
+    particle per unique node, optionally jittered by U(-a, a) H per coordinate."""
+    M = nc
+    pos = np.empty((M * M, 2))
+    ii = np.tile(np.arange(M, dtype=np.float64), M)
+    jj = np.repeat(np.arange(M, dtype=np.float64), M)
+    if a != 0.0:
+        u = uniform01(seed, 2 * M * M)
+        ii = ii + a * (2 * u[0::2] - 1)
+        jj = jj + a * (2 * u[1::2] - 1)
+    x, y = ii / M, jj / M
+    pos[:, 0] = x - np.floor(x)
+    pos[:, 1] = y - np.floor(y)
+    vals = taylor_green(pos)
+    return Problem(f"at_nodes_{nc + 1}", nc + 1, M, a, seed, pos, vals, ["u", "v", "p"])
