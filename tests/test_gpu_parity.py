@@ -291,3 +291,32 @@ def test_particles_recreated_at_nodes(P, a):
             nc = pr.n - 1
             vals = pr.vals.reshape(nc, nc, 3)
             assert np.abs(mesh[:nc, :nc] - vals).max() <= 1e-15
+
+
+def test_large_workload_full_size_sampled(P):
+    """The benchmarked workload at full size (1025^2 mesh, 2048^2 particles, 4 FP32 channels,
+    FP32 solve, the kernels and launch shapes bench.py times): 64 sampled nodes against the
+    oracle node by node, 4096 sampled particles of M2P, and the whole-mesh moment of the
+    round trip.  FP32 error bound: 2e-6 of max|field|."""
+    pr = G.config_large()
+    proj, pos = gpu_setup(P, pr, torch.float32)
+    vals = torch.tensor(pr.vals, dtype=torch.float32, device="cuda")
+    mesh = proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=P.PFEM_SOLVE_F32)
+    back = proj.m2p(pos, mesh)
+    proj.check()
+    m = mesh.cpu().numpy()
+    b = back.cpu().numpy()
+    pos64 = pr.pos.astype(np.float32).astype(np.float64)
+    cells = O.build_cells(pr.n, pos64)
+    rng = np.random.default_rng(21)
+    scale = np.abs(pr.vals).max()
+    worst = 0.0
+    for node in rng.choice(pr.n * pr.n, 64, replace=False):
+        J, I = divmod(int(node), pr.n)
+        idx, w, _, _ = O.node_weights(cells, I, J, 1)
+        worst = max(worst, np.abs(m[J, I] - w @ pr.vals[idx]).max())
+    assert worst / scale < 2e-6, worst / scale
+    sample = rng.choice(pr.N, 4096, replace=False)
+    ref_b = O.m2p(pr.n, pos64[sample], m.astype(np.float64))
+    assert np.abs(b[sample] - ref_b).max() / scale < 2e-6
+    assert np.array_equal(m[-1], m[0]) and np.array_equal(m[:, -1], m[:, 0])
