@@ -71,7 +71,7 @@ namespace pfem {
 void radii_for(int nb, long long N, int *R0, int *rmax, float *dmax)
 {
     radii(nb, N, R0, rmax);
-    *dmax = (float)std::fmin(2.3 * 4294967296.0 / std::sqrt((double)N), 1073741824.0);
+    *dmax = (float)std::fmin(2.0 * 4294967296.0 / std::sqrt((double)N), 1073741824.0);
 }
 }  // namespace pfem
 
@@ -88,7 +88,8 @@ static bool make_geo(int32_t n, int32_t nb, int64_t N, const void *pos_sorted, p
     g->q_sorted = q_sorted;
     g->cell_start = cell_start;
     // first search radius, largest radius, and the distance cutoff of the first star attempt
-    // (2.3 mean particle spacings, fixed point)
+    // (2.0 mean particle spacings, fixed point: above the largest Delaunay circumdiameter of
+    // jittered lattices at jitter 0.25, 1.97 spacings; a star that fails it takes the region search)
     radii_for(nb, N, &g->R0, &g->rmax, &g->dmax);
     // The shared-memory tiled P2M is opt-in: on the jittered-lattice workloads it measured
     // slower than the per-thread kernel (the cost is in the divergent star search, not memory).

@@ -230,7 +230,7 @@ __device__ __forceinline__ int apex_search(const Bins &B, uint2 pv, uint2 pw, co
 #ifndef PFEM_STAR_LIST
 #define PFEM_STAR_LIST 24
 #endif
-constexpr int KL = PFEM_STAR_LIST;   // list capacity (jittered lattices: at most 21 within the cutoff)
+constexpr int KL = PFEM_STAR_LIST;   // list capacity (jittered lattices: at most 17 within 2 spacings)
 
 struct FCirc {
     float K, P, Q, Ka, Pa, Qa;
