@@ -351,15 +351,10 @@ static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, con
     return n >= 3 ? n : -1;
 }
 
-// Counter-clockwise Delaunay star of slot v into nbrs[0..count).  Returns count >= 3, or
-// -PFEM_ERR_* on failure.
-static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
+// Star of v by gift-wrapping over every particle of growing regions (no distance cutoff): the
+// path of a star the list attempt could not certify.
+static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, int R0, int *nbrs)
 {
-    const uint2 pv = __ldg(B.q + v);
-    if (B.dmax > 0.f) {
-        const int c = star_list(B, v, pv, make_region(B, pv, R0), B.dmax, nbrs);
-        if (c != -1) return c;
-    }
     for (int attempt = 1, R = R0; R <= B.rmax; ++attempt, R += attempt > 1 ? 1 : 0) {
         const float dmax = 0.f;
         const Region g = make_region(B, pv, R);
@@ -391,6 +386,18 @@ static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nb
         if (ok && cnt >= 3) return cnt;
     }
     return -PFEM_ERR_CAPACITY;
+}
+
+// Counter-clockwise Delaunay star of slot v into nbrs[0..count), starting at v's nearest
+// neighbour.  Returns count >= 3, or -PFEM_ERR_* on failure.
+static __device__ __noinline__ int star_of(const Bins &B, int v, int R0, int *nbrs)
+{
+    const uint2 pv = __ldg(B.q + v);
+    if (B.dmax > 0.f) {
+        const int c = star_list(B, v, pv, make_region(B, pv, R0), B.dmax, nbrs);
+        if (c != -1) return c;
+    }
+    return star_region(B, v, pv, R0, nbrs);
 }
 
 // Apex left of the directed edge u -> w, searching around u with growing regions.
