@@ -259,7 +259,7 @@ __device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
     return det < -bound ? 1 : (det > bound ? -1 : 0);
 }
 
-static __device__ __noinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
+static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
                                              float D, int *nbrs)
 {
     float2 L[KL];                   // (x, y) relative to v
