@@ -89,7 +89,8 @@ const char *pfem_status_string(pfem_status s);
  * at least 8 bins per side. */
 int32_t pfem_default_bins(int32_t n, int64_t N);
 
-/* Bytes of workspace `ws` needed by the calls below for these sizes (>= 256). */
+/* Bytes of workspace `ws` needed by the calls below for these sizes (>= 256); with n > 0 it
+ * includes room for the quadratic P2M queue of every node (see pfem_project_p2m). */
 size_t pfem_workspace_size(int32_t n, int32_t nb, int64_t N, int32_t C);
 
 /* Status word recorded by device code in `ws` since the last reset; synchronises `stream`
@@ -142,7 +143,9 @@ pfem_status pfem_delaunay_stars(int32_t nb, int64_t N, const uint32_t *q_sorted,
  * w_idx [n*n, K] int32 slot indices (-1 = unused) and w [n*n, K] weights (FP64 when
  * w_t == PFEM_F64, else FP32), so that alpha_i = sum_k w[i,k] alpha[slot w_idx[i,k]].
  * K <= PFEM_KW_MAX; a node with more distinct particles records PFEM_ERR_CAPACITY.
- * Used by the checkpointed backward and by pfem_project_p2m with given weights. */
+ * Used by the checkpointed backward and by pfem_project_p2m with given weights.
+ * Quadratic shape functions: the workspace beyond its first 512 bytes holds a queue of the
+ * nodes the fast solve cannot take (see pfem_project_p2m). */
 pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                  pfem_dtype pos_t, const uint32_t *q_sorted,
                                  const int32_t *cell_start, pfem_shape shape, pfem_solve solve,
@@ -155,7 +158,16 @@ pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *p
  *   w_idx, w  NULL => shape functions computed on the fly (fused); else the weights from
  *             pfem_shape_quadratic (K per node, dtype w_t) are applied
  *   mesh_vals [n, n, C] val_t out
- * C in 1..8. */
+ * C in 1..8.
+ * Quadratic shape functions: each edge's coefficient system (App. B) is solved by a Cholesky
+ * factorisation of its 6x6 moment matrix.  A node with an edge whose pivot falls below the
+ * fast tolerance (rank deficient, e.g. a stencil of five particles, or too ill-conditioned for
+ * the precision: 3e-4 of the trace in FP32, 1e-6 in FP64), or with more than 24 distinct
+ * particles, is queued and recomputed in FP64 with the minimum-norm least-squares solution by
+ * SVD (App. A), by a second kernel on the same stream.  The queue uses the workspace after
+ * its first 512 bytes (8 bytes per queued node, at most n*n): with ws_bytes < 520 there is no
+ * queue and such nodes record PFEM_ERR_DEGENERATE (PFEM_ERR_CAPACITY when the queue is full).
+ * The workspace of pfem_workspace_size() leaves room for every node. */
 pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                              pfem_dtype pos_t, const uint32_t *q_sorted,
                              const int32_t *cell_start, const int32_t *perm, int32_t C,

@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" entry points declared in include/pfem.h: argument checks,
 // workspace layout and dispatch to the kernels.  No entry point allocates device memory.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -17,11 +18,15 @@ void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxe
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Binning scratch for nb*nb bins and N particles; with a mesh (n > 0) the total also covers
+// the P2M queue of nodes for the SVD pass (8 bytes per node after the first 512 bytes), which
+// reuses the binning scratch once the cells are built.
 WsLayout ws_layout(int n, int nb, long long N, int C)
 {
-    (void)n;
     (void)C;
-    return ws_layout_bins((long long)nb * nb, N);
+    WsLayout L = ws_layout_bins((long long)nb * nb, N);
+    if (n > 0) L.total = std::max(L.total, (size_t)512 + 8 * (size_t)n * (size_t)n);
+    return L;
 }
 
 WsLayout ws_layout_bins(long long nbins, long long N)
@@ -193,7 +198,7 @@ pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *p
     if (w_t == PFEM_F32 && pos_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
     if (w_t == PFEM_BF16) return PFEM_ERR_INVALID_ARG;
     if (ws_bytes < 256) return PFEM_ERR_WORKSPACE;
-    return from_cuda(launch_shape(g, shape, solve, K, w_idx, w, w_t, (DevStatus *)ws,
+    return from_cuda(launch_shape(g, shape, solve, K, w_idx, w, w_t, (DevStatus *)ws, ws_bytes,
                                   (cudaStream_t)stream));
 }
 
@@ -222,7 +227,8 @@ pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_s
     // FP64 values use FP64 positions and the FP64 solve; FP32/BF16 values use FP32 positions
     if (val_t == PFEM_F64 && (pos_t != PFEM_F64 || solve != PFEM_SOLVE_F64)) return PFEM_ERR_INVALID_ARG;
     if (val_t != PFEM_F64 && pos_t != PFEM_F32) return PFEM_ERR_INVALID_ARG;
-    return from_cuda(launch_p2m(g, perm, C, vals, val_t, shape, solve, mesh_vals, (DevStatus *)ws, s));
+    return from_cuda(launch_p2m(g, perm, C, vals, val_t, shape, solve, mesh_vals, (DevStatus *)ws,
+                                ws_bytes, s));
 }
 
 pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t, int32_t C,

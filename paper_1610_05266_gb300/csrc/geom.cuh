@@ -295,7 +295,6 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
         int best = -1;
         FCirc cb;
         cb.K = cb.P = cb.Q = cb.Ka = cb.Pa = cb.Qa = 0.f;
-        float lbx = 0.f, lby = 0.f, lbl = 0.f;
         for (int k = 0; k < cnt; ++k) {
             const float2 c2 = L[k];
             const float4 c = make_float4(c2.x, c2.y, fmaf(c2.x, c2.x, c2.y * c2.y), 0.f);
@@ -324,7 +323,6 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
                 if (t < 0) continue;
             }
             best = k;
-            lbx = c.x; lby = c.y; lbl = c.z;
             // circle through v, w, c: K = w x c, P = |c|^2 wy - |w|^2 cy, Q = |w|^2 cx - |c|^2 wx
             const float k1 = wx * c.y, k2 = wy * c.x;
             const float t1 = c.z * wy, t2 = lw * c.y, t3 = lw * c.x, t4 = c.z * wx;
@@ -332,7 +330,6 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
             cb.P = t1 - t2;  cb.Pa = fabsf(t1) + fabsf(t2);
             cb.Q = t3 - t4;  cb.Qa = fabsf(t3) + fabsf(t4);
         }
-        (void)lbx; (void)lby; (void)lbl;
         if (best < 0) return -1;
         // certify: circumcircle centre (-P/2K, -Q/2K), radius |centre|, error margin far above
         // the FP32 rounding of K, P, Q

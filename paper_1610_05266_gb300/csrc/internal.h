@@ -58,9 +58,9 @@ struct GeoArgs {
 
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
                        pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
-                       DevStatus *st, cudaStream_t s);
+                       DevStatus *st, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
-                         void *w, pfem_dtype w_t, DevStatus *st, cudaStream_t s);
+                         void *w, pfem_dtype w_t, DevStatus *st, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_dtype val_t,
                          const int *w_idx, const void *w, int K, pfem_dtype w_t, void *out,
                          cudaStream_t s);

@@ -1,9 +1,24 @@
 // p2m.cu -- launchers of the particle-to-mesh kernels (fused apply, explicit weights, apply
 // from explicit weights) and of the Delaunay-star diagnostic.
+#include <algorithm>
+#include <climits>
+
 #include "internal.h"
 #include "p2m_tiled.cuh"
 
 namespace pfem {
+
+// The queue of nodes for the FP64 SVD pass lives in the workspace after the 256-byte status
+// block: a counter at byte 256, node indices from byte 512.  A workspace of 256 bytes has no
+// queue (such nodes then report PFEM_ERR_DEGENERATE).
+static void set_queue(P2MArgs &a, void *ws, size_t ws_bytes)
+{
+    const long long nodes = (long long)a.n * a.n;
+    const long long cap = ws_bytes >= 520 ? (long long)((ws_bytes - 512) / sizeof(long long)) : 0;
+    a.defer_cap = (int)std::min(std::min(cap, nodes), (long long)INT_MAX);
+    a.defer_count = a.defer_cap > 0 ? (int *)((char *)ws + 256) : nullptr;
+    a.defer_list = a.defer_cap > 0 ? (long long *)((char *)ws + 512) : nullptr;
+}
 
 static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
 {
@@ -43,7 +58,7 @@ int tile_side(int n, int nb, long long N)
 }
 
 template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
-static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0)
+static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s, int T)
 {
     if (!W && T > 0) {
         auto k = k_p2m_tiled<P, V, R, S, REF, SHAPE>;
@@ -60,11 +75,29 @@ static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0)
     return cudaGetLastError();
 }
 
+// Fused P2M: the fast pass over all nodes, then (quadratic shape functions, with a queue) the
+// FP64 SVD pass over the nodes it queued.
+template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
+static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0)
+{
+    const bool queue = SHAPE == PFEM_SHAPE_QUADRATIC && a.defer_cap > 0;
+    if (queue) {
+        cudaError_t e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s, T);
+    if (e != cudaSuccess || !queue) return e;
+    k_p2m_fix<P, V, R, W><<<152, 128, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
                        pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
-                       DevStatus *st, cudaStream_t s)
+                       DevStatus *st, size_t ws_bytes, cudaStream_t s)
 {
     P2MArgs a = make_args(g, st);
+    set_queue(a, st, ws_bytes);
     a.perm = perm;
     a.vals = vals;
     a.C = C;
@@ -88,9 +121,10 @@ cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *val
 }
 
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
-                         void *w, pfem_dtype w_t, DevStatus *st, cudaStream_t s)
+                         void *w, pfem_dtype w_t, DevStatus *st, size_t ws_bytes, cudaStream_t s)
 {
     P2MArgs a = make_args(g, st);
+    set_queue(a, st, ws_bytes);
     a.K = K;
     a.w_idx = w_idx;
     a.w = w;

@@ -27,7 +27,88 @@ struct P2MArgs {
     void *w;                    // [n*n, K]
     int K;
     DevStatus *status;
+    // Queue of nodes whose moment system the fast solve could not factor (rank deficient, or
+    // too ill-conditioned for its precision), recomputed by k_p2m_fix; capacity 0 = no queue.
+    int *defer_count = nullptr;
+    long long *defer_list = nullptr;
+    int defer_cap = 0;
 };
+
+// node_quadratic's code for "queue this node for the FP64 SVD pass" (not a public status), and
+// the marker of a node that was queued.
+constexpr int PFEM_DEFER = 64;
+constexpr int PFEM_DEFERRED = 1;
+
+// A node whose moment system the fast solve could not factor is queued for the FP64 SVD pass
+// (returns PFEM_DEFERRED), or, with no room in the queue, becomes an error code.
+__device__ __forceinline__ int defer_or_error(const P2MArgs &a, int st, long long node)
+{
+    if (st != -PFEM_DEFER) return st;
+    if (a.defer_cap <= 0) return -PFEM_ERR_DEGENERATE;
+    const int i = atomicAdd(a.defer_count, 1);
+    if (i >= a.defer_cap) return -PFEM_ERR_CAPACITY;
+    a.defer_list[i] = node;
+    return PFEM_DEFERRED;
+}
+
+// Minimum-norm least-squares solution of P A = b (App. A: the SVD with rank detection), for the
+// 6 x k matrix P whose columns are the stencil's monomial vectors; pt holds P^T (k rows of 6)
+// and is overwritten.  One-sided (Hestenes) Jacobi: plane rotations of pairs of the six columns
+// of P^T until all are mutually orthogonal, accumulated in V, so that P^T V = W with orthogonal
+// columns w_j = sigma_j u_j.  Then P = V W^T and A = sum_j (v_j . b / sigma_j^2) w_j over the
+// singular values above max(k, 6) eps sigma_max (smaller ones are rank deficiency).
+static __device__ __noinline__ void minnorm_lsq(int k, double (*pt)[6], const double b[6],
+                                                double *A)
+{
+    double V[6][6];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < 5; ++p)
+            for (int q = p + 1; q < 6; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < k; ++i) {
+                    al = fma(pt[i][p], pt[i][p], al);
+                    be = fma(pt[i][q], pt[i][q], be);
+                    ga = fma(pt[i][p], pt[i][q], ga);
+                }
+                if (!(fabs(ga) > 1e-15 * sqrt(al * be))) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int i = 0; i < k; ++i) {
+                    const double x = pt[i][p], y = pt[i][q];
+                    pt[i][p] = c * x - s * y;
+                    pt[i][q] = s * x + c * y;
+                }
+                for (int i = 0; i < 6; ++i) {
+                    const double x = V[i][p], y = V[i][q];
+                    V[i][p] = c * x - s * y;
+                    V[i][q] = s * x + c * y;
+                }
+            }
+        if (!rotated) break;
+    }
+    double sig2[6], vb[6], smax2 = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        double s2 = 0.0, d = 0.0;
+        for (int i = 0; i < k; ++i) s2 = fma(pt[i][j], pt[i][j], s2);
+        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
+        sig2[j] = s2;
+        vb[j] = d;
+        smax2 = fmax(smax2, s2);
+    }
+    const double tol = (double)(k > 6 ? k : 6) * 2.220446049250313e-16;
+    const double thr2 = tol * tol * smax2;
+    for (int i = 0; i < k; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < 6; ++j)
+            if (sig2[j] > thr2) a = fma(vb[j] / sig2[j], pt[i][j], a);
+        A[i] = a;
+    }
+}
 
 // Node position and minimal-image offsets in the compute precision R.
 template <typename P, typename R> struct NodePos;
@@ -116,17 +197,6 @@ __device__ __forceinline__ void store_vals<float, float>(float *out, long long n
         if (c < C) out[node * C + c] = acc[c];
 }
 
-__device__ __forceinline__ bool in_list(const int *lst, int n, int x)
-{
-    for (int i = 0; i < n; ++i)
-        if (lst[i] == x) return true;
-    return false;
-}
-
-// Coefficients A_{mu e} of edge e = (nu, sg) over S_e = {nu} + star(nu) + star(sg) (each
-// particle once; sg is in star(nu), nu in star(sg)).  Calls emit(slot, coef * A_mu) for every
-// stencil member.  S is the solve precision; REFINE adds one refinement step with an FP64
-// residual.  Returns false when the moment matrix is numerically singular.
 // A star as a list of slots: plain slot array (per-thread path) or shared-memory indices
 // mapped to slots (tiled path).
 struct ArrStar {
@@ -135,118 +205,34 @@ struct ArrStar {
     __device__ __forceinline__ int operator[](int i) const { return p[i]; }
 };
 
-template <typename SA> __device__ __forceinline__ bool star_has(const SA &st, int x)
-{
-    for (int i = 0; i < st.n; ++i)
-        if (st[i] == x) return true;
-    return false;
-}
-
-template <typename P, typename R, typename S, bool REFINE, typename SA, typename Emit>
-__device__ __forceinline__ bool edge_weights_sa(const P2MArgs &a, const NodePos<P, R> &np, int nu,
-                                                int sg, const SA &st_nu, const SA &st_sg, R coef,
-                                                Emit &&emit)
-{
-    const int n_nu = st_nu.n, n_sg = st_sg.n;
-    R rnx, rny, rsx, rsy;
-    np.off(a.pos, nu, rnx, rny);
-    np.off(a.pos, sg, rsx, rsy);
-    const S mx = (S(rnx) + S(rsx)) * S(0.5), my = (S(rny) + S(rsy)) * S(0.5);
-    const S ex = S(rnx) - S(rsx), ey = S(rny) - S(rsy);
-    const S inv = S(1) / sqrt(ex * ex + ey * ey);
-
-    // visit every stencil member once: nu, star(nu), then star(sg) minus {nu} + star(nu)
-    auto for_stencil = [&](auto &&f) {
-        f(nu);
-        for (int i = 0; i < n_nu; ++i) f(st_nu[i]);
-        for (int j = 0; j < n_sg; ++j) {
-            const int m = st_sg[j];
-            if (m == nu || star_has(st_nu, m)) continue;
-            f(m);
-        }
-    };
-    auto coords = [&](int s, S &x, S &y) {
-        R dx, dy;
-        np.off(a.pos, s, dx, dy);
-        x = (S(dx) - mx) * inv;
-        y = (S(dy) - my) * inv;
-    };
-
-    Moment<S> M;
-    M.zero();
-    for_stencil([&](int s) {
-        S x, y;
-        coords(s, x, y);
-        M.add(x, y);
-    });
-    if (!M.factor(SolveTol<S>::v)) return false;
-    const S tx = ex * inv, ty = ey * inv;
-    const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
-    S y[6];
-    M.solve(b, y);
-    if (REFINE) {
-        // r = b - (sum p p^T) y with p from the same FP32 coordinates, accumulated in FP64
-        double r[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) r[i] = (double)b[i];
-        for_stencil([&](int s) {
-            S x, y2;
-            coords(s, x, y2);
-            const double X = x, Y = y2;
-            const double p[6] = {1.0, X, Y, X * X, X * Y, Y * Y};
-            double t = 0.0;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) t = fma(p[i], (double)y[i], t);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) r[i] = fma(-p[i], t, r[i]);
-        });
-        S rs[6], dy[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) rs[i] = (S)r[i];
-        M.solve(rs, dy);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) y[i] += dy[i];
-    }
-    for_stencil([&](int s) {
-        S x, y2;
-        coords(s, x, y2);
-        const S A = y[0] + x * y[1] + y2 * y[2] + x * x * y[3] + x * y2 * y[4] + y2 * y2 * y[5];
-        emit(s, coef * R(A));
-    });
-    return true;
-}
-
-template <typename P, typename R, typename S, bool REFINE, typename Emit>
-__device__ __forceinline__ bool edge_weights(const P2MArgs &a, const NodePos<P, R> &np, int nu,
-                                             int sg, const int *st_nu, int n_nu,
-                                             const int *st_sg, int n_sg, R coef, Emit &&emit)
-{
-    return edge_weights_sa<P, R, S, REFINE>(a, np, nu, sg, ArrStar{st_nu, n_nu},
-                                            ArrStar{st_sg, n_sg}, coef, emit);
-}
-
 // Quadratic weights of one node over its distinct particles U = T + stars of T's vertices:
 // offsets are loaded once per particle, each edge's stencil is a bit mask over U, and
 // w_u = lambda_u [u in T] + sum_e 2 lambda_nu lambda_sg A_{u e} accumulates per particle.
-// Calls emit(slot, w) once per particle of U.  Returns 0, or -PFEM_ERR_* (singular moment
-// matrix, or more than 32 distinct particles).
-constexpr int UMAX = 24;
+// Calls emit(slot, w) once per particle of U.  Returns 0, -PFEM_DEFER (a moment matrix the
+// Cholesky solve cannot factor, or more than UMAX distinct particles: queue the node for the
+// SVD pass) or, in the SVD pass, -PFEM_ERR_CAPACITY (more than UMAX_SVD distinct particles).
+constexpr int UMAX = 24;       // fast pass: jittered lattices have at most about 20
+constexpr int UMAX_SVD = 32;   // SVD pass (the stencil masks are 32-bit)
 
-template <typename P, typename R, typename S, bool REFINE, typename SA, typename Emit>
+// SVD = true (the FP64 pass over queued nodes): each edge's coefficients are the minimum-norm
+// least-squares solution by SVD instead of the Cholesky solve of the moment system.
+template <typename P, typename R, typename S, bool REFINE, bool SVD = false, typename SA,
+          typename Emit>
 __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
                                               const int tri[3], const SA *st, const R lam[3],
                                               Emit &&emit)
 {
     // Only the slots and weights are kept per thread: offsets are re-read from the positions,
     // which neighbouring nodes share in L1, instead of being copied into thread-private memory.
-    int us[UMAX];
-    R uw[UMAX];
+    constexpr int UM = SVD ? UMAX_SVD : UMAX;
+    int us[UM];
+    R uw[UM];
     int nu = 0;
     bool over = false;
     auto add = [&](int s) -> int {
         for (int i = 0; i < nu; ++i)
             if (us[i] == s) return i;
-        if (nu == UMAX) { over = true; return 0; }
+        if (nu == UM) { over = true; return 0; }
         us[nu] = s;
         uw[nu] = R(0);
         return nu++;
@@ -270,7 +256,7 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         for (int i = 0; i < st[e].n; ++i) m |= 1u << add(st[e][i]);
         vm[e] = m;
     }
-    if (over) return -PFEM_ERR_CAPACITY;
+    if (over) return SVD ? -PFEM_ERR_CAPACITY : -PFEM_DEFER;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const int f = e == 2 ? 0 : e + 1;
@@ -281,6 +267,27 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
         const S ex = rnx - rsx, ey = rny - rsy;
         const S inv = S(1) / sqrt(ex * ex + ey * ey);
+        if constexpr (SVD) {
+            double pt[UM][6];
+            int ids[UM];
+            int k = 0;
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int i = __ffs(m) - 1;
+                S ox, oy;
+                offset(i, ox, oy);
+                const double x = (double)((ox - mx) * inv), y = (double)((oy - my) * inv);
+                pt[k][0] = 1.0; pt[k][1] = x; pt[k][2] = y;
+                pt[k][3] = x * x; pt[k][4] = x * y; pt[k][5] = y * y;
+                ids[k++] = i;
+            }
+            const double tx = (double)(ex * inv), ty = (double)(ey * inv);
+            const double b[6] = {0.0, 0.0, 0.0, -0.5 * tx * tx, -0.5 * tx * ty, -0.5 * ty * ty};
+            double A[UM];
+            minnorm_lsq(k, pt, b, A);
+            const double coef = 2.0 * (double)lam[e] * (double)lam[f];
+            for (int j = 0; j < k; ++j) uw[ids[j]] += (R)(coef * A[j]);
+            continue;
+        }
         Moment<S> M;
         M.zero();
         for (unsigned m = mask; m; m &= m - 1) {
@@ -289,7 +296,7 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
             offset(i, ox, oy);
             M.add((ox - mx) * inv, (oy - my) * inv);
         }
-        if (!M.factor(SolveTol<S>::v)) return -PFEM_ERR_DEGENERATE;
+        if (!M.factor(FastTol<S>::v)) return -PFEM_DEFER;
         const S tx = ex * inv, ty = ey * inv;
         const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
         S y[6];
@@ -337,7 +344,8 @@ template <> __device__ __forceinline__ double nan_of<double>() { return __longlo
 
 // One mesh node.  WEIGHTS = false: write alpha_i for all C components; true: write the
 // node's distinct (slot, weight) pairs.
-template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS>
+template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS,
+          bool SVD = false>
 __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
 {
     const int nc = a.n - 1;
@@ -383,13 +391,14 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
         if (st == 0) {
             if (SHAPE == PFEM_SHAPE_QUADRATIC) {
                 const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
-                st = node_quadratic<P, R, S, REFINE>(a, np, tri, sa, lam, emit);
+                st = node_quadratic<P, R, S, REFINE, SVD>(a, np, tri, sa, lam, emit);
             } else {
                 for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
             }
         }
+        st = defer_or_error(a, st, node);
         if (st != 0) {
-            record_error(a.status, -st, node);
+            if (st < 0) record_error(a.status, -st, node);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
         }
@@ -408,14 +417,15 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
         if (st == 0) {
             if (SHAPE == PFEM_SHAPE_QUADRATIC) {
                 const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
-                st = node_quadratic<P, R, S, REFINE>(a, np, tri, sa, lam, emit);
+                st = node_quadratic<P, R, S, REFINE, SVD>(a, np, tri, sa, lam, emit);
             } else {
                 for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
             }
             if (over && st == 0) st = -PFEM_ERR_CAPACITY;
         }
+        st = defer_or_error(a, st, node);
         if (st != 0) {
-            record_error(a.status, -st, node);
+            if (st < 0) record_error(a.status, -st, node);
             cnt = 0;
         }
         int *oi = a.w_idx + node * a.K;
@@ -441,6 +451,21 @@ __global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m(P2MArgs a)
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
     if (I >= a.n || J >= a.n) return;
     p2m_node<P, V, R, S, REFINE, SHAPE, WEIGHTS>(a, I, J);
+}
+
+// The queued nodes again, in FP64 with the SVD solve of every edge, overwriting the fast pass's
+// placeholder output.  A node that fails here reports its error.
+template <typename P, typename V, typename R, bool WEIGHTS>
+__global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
+{
+    const int cnt = min(*a.defer_count, a.defer_cap);
+    P2MArgs f = a;
+    f.defer_cap = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const long long node = a.defer_list[i];
+        p2m_node<P, V, R, double, false, PFEM_SHAPE_QUADRATIC, WEIGHTS, true>(
+            f, (int)(node % a.n), (int)(node / a.n));
+    }
 }
 
 }  // namespace pfem

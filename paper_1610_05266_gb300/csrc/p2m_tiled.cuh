@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(TT, 2) k_p2m_tiled(P2MArgs a, int T, int tiles
                         for (int step = 0; step < 64 && !done && !fallback; ++step) {
                             SRegion g;
                             int x = -1;
-                            for (int R = a.R0; R <= a.B.rmax && x < 0; ++R) {
-                                if (!sregion(S, nb, S.rq[e1], R, g)) break;
+                            for (int Rr = a.R0; Rr <= a.B.rmax && x < 0; ++Rr) {
+                                if (!sregion(S, nb, S.rq[e1], Rr, g)) break;
                                 x = apex_smem(S, S.rq[e1], S.rq[e0], g);
                             }
                             if (x < 0) { fallback = true; break; }
@@ -441,8 +441,9 @@ __global__ void __launch_bounds__(TT, 2) k_p2m_tiled(P2MArgs a, int T, int tiles
     } else {
         for (int e = 0; e < 3; ++e) emit(gt[e], lam[e]);
     }
+    err = defer_or_error(a, err, node);
     if (err) {
-        record_error(a.status, -err, node);
+        if (err < 0) record_error(a.status, -err, node);
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
     }
