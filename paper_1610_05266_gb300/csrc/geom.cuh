@@ -259,11 +259,12 @@ __device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
     return det < -bound ? 1 : (det > bound ? -1 : 0);
 }
 
+template <int KLC = KL>
 static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
                                              float D, int *nbrs)
 {
-    float2 L[KL];                   // (x, y) relative to v
-    int Ls[KL];                     // slots
+    float2 L[KLC];                  // (x, y) relative to v
+    int Ls[KLC];                    // slots
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
     bool dup = false, over = false;
@@ -276,7 +277,7 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
         if (l > D2) return;
         const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
         dup |= d2 == 0;
-        if (cnt == KL) { over = true; return; }
+        if (cnt == KLC) { over = true; return; }
         L[cnt] = make_float2(fx, fy);
         Ls[cnt] = s;
         if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; }
@@ -352,6 +353,18 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
 // path of a star the list attempt could not certify.
 static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, int R0, int *nbrs)
 {
+    // First a list attempt with a 1.75 times larger cutoff and a 64-entry list over the bins
+    // that cover it (irregular particle sets: on uniform random particles 44 % of the stars
+    // have a circumcircle wider than 2 mean spacings, 0.3 % wider than 3.5).
+    if (B.dmax > 0.f) {
+        const float D2 = B.dmax * 1.75f;
+        const float bw = 4294967296.0f / (float)B.nb;
+        const int R2 = (int)ceilf(D2 / bw);
+        if (R2 <= B.rmax) {
+            const int c = star_list<64>(B, v, pv, make_region(B, pv, R2 > R0 ? R2 : R0), D2, nbrs);
+            if (c != -1) return c;
+        }
+    }
     for (int attempt = 1, R = R0; R <= B.rmax; ++attempt, R += attempt > 1 ? 1 : 0) {
         const float dmax = 0.f;
         const Region g = make_region(B, pv, R);
