@@ -378,6 +378,18 @@ def run_ours(args, world, rank, local):
     side["fp64_round_trip_ms"] = t64
     side["fp64_round_trip_mparticles_s"] = N / (t64 * 1e-3) / 1e6
     proj64.check("fp64 round trip")
+    # irregular input: uniform random particles (no lattice), same sizes, FP32 quadratic P2M
+    from workloads import generators as WG
+    pos_u = torch.tensor(WG.uniform01(WG.SEED_BASE + 62, 2 * N).reshape(N, 2), dtype=torch.float32,
+                         device=dev)
+    proj_u = P.Projector(n, N, C=C, pos_dtype=torch.float32, device=dev)
+    proj_u.build(pos_u)
+    side["uniform_random_p2m_linear_ms"] = timeit(
+        lambda: proj_u.p2m(vals, shape=P.PFEM_SHAPE_LINEAR, out=mesh), reps=3)
+    side["uniform_random_p2m_quadratic_ms"] = timeit(
+        lambda: proj_u.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=solve, out=mesh), reps=3)
+    side["uniform_random_status"] = int(proj_u.status()[0])
+    del proj_u, pos_u
     out["side"] = side
 
     # --- differentiation workload: L = 1/2 sum_i (P2M_i - t_i)^2, backward to values and
