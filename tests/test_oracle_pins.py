@@ -186,6 +186,35 @@ def test_edge_constraints_and_min_norm(tiny):
             assert np.abs(A - A_ref).max() < 1e-9 * max(1.0, np.abs(A_ref).max())
 
 
+def test_rank_deficient_edge_is_the_pseudo_inverse_solution():
+    """A rank-deficient edge system (App. A: SVD with rank detection).  In 2048^2 uniform
+    random particles, node (245, 118) lies in a triangle with a 0.08-spacing edge whose
+    stencil has five particles: six conditions, five unknowns, rank 5.  The oracle's A must
+    be LAPACK's pseudo-inverse solution: the least-squares optimum (P^T (P A - b) = 0, the
+    conditions cannot all hold) of minimum norm."""
+    N = 2048 * 2048
+    pos = G.uniform01(G.SEED_BASE + 62, 2 * N).reshape(N, 2)
+    cells = O.build_cells(1025, pos)
+    I, J = 245, 118
+    tri, lam, edges, ranks = O.node_edges(cells, I, J)
+    e = int(np.argmin(ranks))
+    S, A = edges[e]
+    assert ranks[e] == 5 and len(S) == 5
+    nu, sg = tri[e], tri[(e + 1) % 3]
+    d = offsets(pos, S, 1025, I, J)
+    dn = offsets(pos, np.array([nu]), 1025, I, J)[0]
+    ds = offsets(pos, np.array([sg]), 1025, I, J)[0]
+    mid, L = 0.5 * (dn + ds), np.linalg.norm(dn - ds)
+    x = (d - mid) / L                                  # the frame does not change A (eq. A2_2)
+    t = (dn - ds) / L
+    P = np.stack([np.ones(len(S)), x[:, 0], x[:, 1], x[:, 0] ** 2, x[:, 0] * x[:, 1], x[:, 1] ** 2])
+    b = np.array([0, 0, 0, -0.5 * t[0] ** 2, -0.5 * t[0] * t[1], -0.5 * t[1] ** 2])
+    A_ref = np.linalg.pinv(P) @ b
+    assert np.abs(A - A_ref).max() < 1e-9 * max(1.0, np.abs(A_ref).max())
+    assert np.abs(P.T @ (P @ A - b)).max() < 1e-12
+    assert np.abs(P @ A - b).max() > 1e-6               # inconsistent: least squares, not exact
+
+
 def test_interpolating_property(tiny):
     """A node that coincides with a particle takes that particle's value (App. B: the
     extended functions stay interpolating)."""
