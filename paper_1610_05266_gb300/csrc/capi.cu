@@ -19,13 +19,13 @@ void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxe
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Binning scratch for nb*nb bins and N particles; with a mesh (n > 0) the total also covers
-// the P2M queue of nodes for the SVD pass (8 bytes per node after the first 512 bytes), which
-// reuses the binning scratch once the cells are built.
+// what quadratic P2M keeps in the workspace once the cells are built (the queue of nodes for
+// the SVD pass and the per-node records of the two-kernel path).
 WsLayout ws_layout(int n, int nb, long long N, int C)
 {
     (void)C;
     WsLayout L = ws_layout_bins((long long)nb * nb, N);
-    if (n > 0) L.total = std::max(L.total, (size_t)512 + 8 * (size_t)n * (size_t)n);
+    if (n > 0) L.total = std::max(L.total, p2m_ws_bytes((long long)n * n));
     return L;
 }
 

@@ -59,6 +59,8 @@ struct GeoArgs {
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
                        pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
                        DevStatus *st, size_t ws_bytes, cudaStream_t s);
+// Workspace bytes quadratic P2M uses for n*n nodes (queue + node records of the two-kernel path).
+size_t p2m_ws_bytes(long long nodes);
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
                          void *w, pfem_dtype w_t, DevStatus *st, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_dtype val_t,

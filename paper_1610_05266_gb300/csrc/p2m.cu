@@ -75,17 +75,60 @@ static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s, int T)
     return cudaGetLastError();
 }
 
-// Fused P2M: the fast pass over all nodes, then (quadratic shape functions, with a queue) the
-// FP64 SVD pass over the nodes it queued.
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout of quadratic P2M after the 256-byte status block: the queue counter at 256,
+// the queue from 512 (8 bytes per node), then the node records of the two-kernel path.
+static size_t recs_offset(long long nodes) { return al256(512 + 8 * (size_t)nodes); }
+
+size_t p2m_ws_bytes(long long nodes)
+{
+    size_t off = recs_offset(nodes);
+    off = al256(off + sizeof(int) * (size_t)nodes);
+    off = al256(off + 3 * sizeof(unsigned) * (size_t)nodes);
+    off = al256(off + 3 * sizeof(double) * (size_t)nodes);
+    return off + UMAX * sizeof(int) * (size_t)nodes;
+}
+
+static bool set_recs(NodeRecs &r, void *ws, size_t ws_bytes, long long nodes)
+{
+    if (ws_bytes < p2m_ws_bytes(nodes)) return false;
+    char *b = (char *)ws;
+    size_t off = recs_offset(nodes);
+    r.meta = (int *)(b + off);
+    off = al256(off + sizeof(int) * (size_t)nodes);
+    r.mask = (unsigned *)(b + off);
+    off = al256(off + 3 * sizeof(unsigned) * (size_t)nodes);
+    r.lam = (double *)(b + off);
+    off = al256(off + 3 * sizeof(double) * (size_t)nodes);
+    r.us = (int *)(b + off);
+    r.nodes = nodes;
+    return true;
+}
+
+// Fused P2M: the fast pass over all nodes (one kernel, or with node records the geometry and
+// solve kernels), then (quadratic shape functions, with a queue) the FP64 SVD pass over the
+// nodes it queued.
 template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
-static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0)
+static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0, const NodeRecs *rec = nullptr)
 {
     const bool queue = SHAPE == PFEM_SHAPE_QUADRATIC && a.defer_cap > 0;
     if (queue) {
         cudaError_t e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s, T);
+    cudaError_t e;
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && T == 0 && rec) {
+        k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *rec);
+        count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_p2m_solve<P, V, R, S, REF><<<(unsigned)((rec->nodes + 127) / 128), 128, 0, s>>>(a, *rec);
+        count_launch();
+        e = cudaGetLastError();
+    } else {
+        e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s, T);
+    }
     if (e != cudaSuccess || !queue) return e;
     k_p2m_fix<P, V, R, W><<<152, 128, 0, s>>>(a);
     count_launch();
@@ -104,20 +147,22 @@ cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *val
     a.out = out;
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
     const int T = g.tiled ? tile_side(g.n, g.nb, g.N) : 0;
+    NodeRecs recs;
+    const NodeRecs *r = set_recs(recs, st, ws_bytes, (long long)g.n * g.n) ? &recs : nullptr;
     if (val_t == PFEM_F64) {   // positions FP64, arithmetic FP64
         if (!q) return go<double, double, double, double, false, 0, false>(a, s, T);
-        return go<double, double, double, double, false, 1, false>(a, s, T);
+        return go<double, double, double, double, false, 1, false>(a, s, T, r);
     }
     if (val_t == PFEM_F32) {   // positions FP32, arithmetic FP32
         if (!q) return go<float, float, float, float, false, 0, false>(a, s, T);
-        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s, T);
-        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s, T);
-        return go<float, float, float, float, true, 1, false>(a, s, T);
+        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s, T, r);
+        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s, T, r);
+        return go<float, float, float, float, true, 1, false>(a, s, T, r);
     }
     if (!q) return go<float, __nv_bfloat16, float, float, false, 0, false>(a, s, T);
-    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s, T);
-    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s, T);
-    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s, T);
+    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s, T, r);
+    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s, T, r);
+    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s, T, r);
 }
 
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,

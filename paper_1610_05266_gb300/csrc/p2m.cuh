@@ -216,18 +216,15 @@ constexpr int UMAX_SVD = 32;   // SVD pass (the stencil masks are 32-bit)
 
 // SVD = true (the FP64 pass over queued nodes): each edge's coefficients are the minimum-norm
 // least-squares solution by SVD instead of the Cholesky solve of the moment system.
-template <typename P, typename R, typename S, bool REFINE, bool SVD = false, typename SA,
-          typename Emit>
-__device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
-                                              const int tri[3], const SA *st, const R lam[3],
-                                              Emit &&emit)
+// The node's distinct particles U = T + stars of T's vertices (slots us[0..nu)), the stencil
+// of the edge (tri[e], tri[e+1]) as the bit mask vm[e] | vm[e+1] over U, vi[e] the index of
+// tri[e] in U, and uw initialised to the linear weights lambda.  Returns 0, or -1 when U has
+// more than UM particles.
+template <int UM, typename R, typename SA>
+__device__ __forceinline__ int node_u_build(const int tri[3], const SA *st, const R lam[3],
+                                            int *us, R *uw, int &nu, unsigned vm[3], int vi[3])
 {
-    // Only the slots and weights are kept per thread: offsets are re-read from the positions,
-    // which neighbouring nodes share in L1, instead of being copied into thread-private memory.
-    constexpr int UM = SVD ? UMAX_SVD : UMAX;
-    int us[UM];
-    R uw[UM];
-    int nu = 0;
+    nu = 0;
     bool over = false;
     auto add = [&](int s) -> int {
         for (int i = 0; i < nu; ++i)
@@ -237,14 +234,6 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         uw[nu] = R(0);
         return nu++;
     };
-    auto offset = [&](int i, S &x, S &y) {
-        R dx, dy;
-        np.off(a.pos, us[i], dx, dy);
-        x = S(dx);
-        y = S(dy);
-    };
-    unsigned vm[3];
-    int vi[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         vi[e] = add(tri[e]);
@@ -256,7 +245,24 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
         for (int i = 0; i < st[e].n; ++i) m |= 1u << add(st[e][i]);
         vm[e] = m;
     }
-    if (over) return SVD ? -PFEM_ERR_CAPACITY : -PFEM_DEFER;
+    return over ? -1 : 0;
+}
+
+// The three edge systems of a node over its particle set: uw[u] += 2 lambda_nu lambda_sg A_{u e}.
+// Returns 0, or -PFEM_DEFER when a moment matrix is below the fast-solve tolerance.
+template <typename P, typename R, typename S, bool REFINE, bool SVD, int UM>
+__device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R> &np,
+                                            const int *us, R *uw, const unsigned vm[3],
+                                            const int vi[3], const R lam[3])
+{
+    // Offsets are re-read from the positions, which neighbouring nodes share in L1, instead of
+    // being copied into thread-private memory.
+    auto offset = [&](int i, S &x, S &y) {
+        R dx, dy;
+        np.off(a.pos, us[i], dx, dy);
+        x = S(dx);
+        y = S(dy);
+    };
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const int f = e == 2 ? 0 : e + 1;
@@ -334,8 +340,41 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
             uw[i] = fma(coef, R(A), uw[i]);
         }
     }
+    return 0;
+}
+
+template <typename P, typename R, typename S, bool REFINE, bool SVD = false, typename SA,
+          typename Emit>
+__device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
+                                              const int tri[3], const SA *st, const R lam[3],
+                                              Emit &&emit)
+{
+    constexpr int UM = SVD ? UMAX_SVD : UMAX;
+    int us[UM];
+    R uw[UM];
+    int nu;
+    unsigned vm[3];
+    int vi[3];
+    if (node_u_build<UM>(tri, st, lam, us, uw, nu, vm, vi) != 0)
+        return SVD ? -PFEM_ERR_CAPACITY : -PFEM_DEFER;
+    const int r = node_u_solve<P, R, S, REFINE, SVD, UM>(a, np, us, uw, vm, vi, lam);
+    if (r != 0) return r;
     for (int i = 0; i < nu; ++i) emit(us[i], uw[i]);
     return 0;
+}
+
+// Barycentric coordinates of the node (the origin of np's offsets) in triangle tri.
+template <typename P, typename R>
+__device__ __forceinline__ void barycentric(const P2MArgs &a, const NodePos<P, R> &np,
+                                            const int tri[3], R lam[3])
+{
+    R d[3][2];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
+    const R area2 = (d[1][0] - d[0][0]) * (d[2][1] - d[0][1]) - (d[1][1] - d[0][1]) * (d[2][0] - d[0][0]);
+    lam[0] = (d[1][0] * d[2][1] - d[1][1] * d[2][0]) / area2;
+    lam[1] = (d[2][0] * d[0][1] - d[2][1] * d[0][0]) / area2;
+    lam[2] = (d[0][0] * d[1][1] - d[0][1] * d[1][0]) / area2;
 }
 
 template <typename V> __device__ __forceinline__ V nan_of();
@@ -367,15 +406,7 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
     NodePos<P, R> np;
     np.init(Iu, Ju, nc);
     R lam[3] = {R(0), R(0), R(0)};
-    if (st == 0) {
-        R d[3][2];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
-        const R area2 = (d[1][0] - d[0][0]) * (d[2][1] - d[0][1]) - (d[1][1] - d[0][1]) * (d[2][0] - d[0][0]);
-        lam[0] = (d[1][0] * d[2][1] - d[1][1] * d[2][0]) / area2;
-        lam[1] = (d[2][0] * d[0][1] - d[2][1] * d[0][0]) / area2;
-        lam[2] = (d[0][0] * d[1][1] - d[0][1] * d[1][0]) / area2;
-    }
+    if (st == 0) barycentric(a, np, tri, lam);
 
     if (!WEIGHTS) {
         R acc[8];
@@ -466,6 +497,128 @@ __global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
         p2m_node<P, V, R, double, false, PFEM_SHAPE_QUADRATIC, WEIGHTS, true>(
             f, (int)(node % a.n), (int)(node / a.n));
     }
+}
+
+// ---------------------------------------------------------------- two-kernel fused P2M
+// The quadratic apply path as two kernels, so that the star search (large thread-private
+// state, latency bound) and the moment solves (register-heavy arithmetic) each get their own
+// register budget: k_p2m_geom locates the node and builds its particle set, k_p2m_solve
+// solves the three edge systems and applies the weights.  They hand over a per-node record,
+// one array per field so that both kernels access it coalesced.
+struct NodeRecs {
+    int *meta;          // [nodes] nu | vi0 << 5 | vi1 << 10 | vi2 << 15, or -1: no record
+    unsigned *mask;     // [3][nodes] vm[e]
+    double *lam;        // [3][nodes] barycentric coordinates (exact in both precisions)
+    int *us;            // [UMAX][nodes] slots of the particle set
+    long long nodes;
+};
+
+__host__ __device__ constexpr size_t node_recs_bytes_per_node()
+{
+    return sizeof(int) + 3 * sizeof(unsigned) + 3 * sizeof(double) + UMAX * sizeof(int);
+}
+
+template <typename P, typename V, typename R>
+__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
+    const int nc = a.n - 1;
+    const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+    const long long node = (long long)J * a.n + I;
+    const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+    int tri[3];
+    int stars[3][KMAX];
+    int ns[3] = {0, 0, 0};
+    int st = locate(a.B, qn, a.R0, tri, stars[0], ns[0]);
+    for (int e = 0; e < 3 && st == 0; ++e)
+        if (ns[e] == 0) {
+            const int c = star_of(a.B, tri[e], a.R0, stars[e]);
+            if (c < 0) st = c;
+            else ns[e] = c;
+        }
+    int meta = -1;
+    if (st == 0) {
+        NodePos<P, R> np;
+        np.init(Iu, Ju, nc);
+        R lam[3];
+        barycentric(a, np, tri, lam);
+        int us[UMAX];
+        R uw[UMAX];
+        int nu;
+        unsigned vm[3];
+        int vi[3];
+        const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
+        if (node_u_build<UMAX>(tri, sa, lam, us, uw, nu, vm, vi) != 0) {
+            st = -PFEM_DEFER;
+        } else {
+            for (int i = 0; i < nu; ++i) r.us[i * r.nodes + node] = us[i];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                r.mask[e * r.nodes + node] = vm[e];
+                r.lam[e * r.nodes + node] = (double)lam[e];
+            }
+            meta = nu | vi[0] << 5 | vi[1] << 10 | vi[2] << 15;
+        }
+    }
+    r.meta[node] = meta;
+    if (st != 0) {
+        st = defer_or_error(a, st, node);
+        if (st < 0) record_error(a.status, -st, node);
+        R acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+        store_vals<V, R>((V *)a.out, node, a.C, acc);
+    }
+}
+
+template <typename P, typename V, typename R, typename S, bool REFINE>
+__global__ void __launch_bounds__(128, 8) k_p2m_solve(P2MArgs a, NodeRecs r)
+{
+    const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (node >= r.nodes) return;
+    const int meta = r.meta[node];
+    if (meta < 0) return;
+    const int nu = meta & 31;
+    const int vi[3] = {(meta >> 5) & 31, (meta >> 10) & 31, (meta >> 15) & 31};
+    int us[UMAX];
+    R uw[UMAX];
+    for (int i = 0; i < nu; ++i) {
+        us[i] = r.us[i * r.nodes + node];
+        uw[i] = R(0);
+    }
+    unsigned vm[3];
+    R lam[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        vm[e] = r.mask[e * r.nodes + node];
+        lam[e] = (R)r.lam[e * r.nodes + node];
+        uw[vi[e]] += lam[e];
+    }
+    const int nc = a.n - 1;
+    const int I = (int)(node % a.n), J = (int)(node / a.n);
+    NodePos<P, R> np;
+    np.init(I == nc ? 0 : I, J == nc ? 0 : J, nc);
+    int st = node_u_solve<P, R, S, REFINE, false, UMAX>(a, np, us, uw, vm, vi, lam);
+    R acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = R(0);
+    if (st == 0) {
+        for (int i = 0; i < nu; ++i) {
+            R v[8];
+            load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < a.C) acc[c] = fma(uw[i], v[c], acc[c]);
+        }
+    } else {
+        st = defer_or_error(a, st, node);
+        if (st < 0) record_error(a.status, -st, node);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+    }
+    store_vals<V, R>((V *)a.out, node, a.C, acc);
 }
 
 }  // namespace pfem
