@@ -14,6 +14,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -26,17 +27,20 @@ METRIC = "Mparticles/s for P2M+M2P round trip; %HBM peak; max rel err vs FP64 or
 UNIT = "Mparticles/s"
 L2_BYTES = 129 * 1024 * 1024
 
-# FP32 arithmetic of the quadratic P2M per node ("roofline"): barycentrics
-# (30) + 3 edges x (244 + 77 k) with mean stencil size k = 10, + linear apply (24), C = 4.
+# FP32 arithmetic the method defines for one node of the quadratic P2M (the Delaunay search is
+# integer and filtered-predicate work, not counted): barycentrics (30) + 3 edges x (244 + 77 k)
+# with mean stencil size k = 10 (frame, Cholesky, two triangular solves; per stencil point the
+# coordinates, monomials, moment update, coefficient and the apply of C = 4 values), + 24.
 FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * 10) + 24
 FP32_LANES = 152 * 128
 
 
 def p2m_traffic():
-    """DRAM bytes of one k_p2m launch from the committed ncu summary, or None when the kernel
-    sources changed since those counters were taken."""
+    """DRAM bytes of one quadratic P2M call (its geometry, solve and SVD-pass kernels) from the
+    committed ncu summary, or None when the kernel sources changed since those counters were
+    taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_p2m_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_p2m_geom_solve_traffic.txt")
     try:
         kv = dict(line.split()[:2] for line in open(path) if line.strip() and not line.startswith("#"))
     except Exception:
@@ -95,7 +99,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"pfem_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -289,12 +293,12 @@ def run_ours(args, world, rank, local):
                       "channels": C, "jitter": pr.a, "shape": "quadratic", "solve": args.solve,
                       "bins": proj.nb, "l2": "flushed between timed steps (2x L2 write)",
                       "parallelism": "replicas only" if world > 1 else "single GPU"},
-           "roofline": {"bound": "alu", "kernel": "k_p2m (fused quadratic P2M)",
+           "roofline": {"bound": "alu", "kernel": "quadratic P2M (k_p2m_geom + k_p2m_solve)",
                         "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak,
                         "unit": "TFLOP/s",
                         "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
                         "traffic": p2m_traffic(),
-                        "traffic_unit": "bytes per launch (ncu dram read+write)",
+                        "traffic_unit": "bytes per P2M call (ncu dram read+write, summed over its kernels)",
                         "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
            "hbm_view": {"round_trip_bytes": rt_bytes,

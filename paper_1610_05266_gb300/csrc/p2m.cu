@@ -106,8 +106,8 @@ static bool set_recs(NodeRecs &r, void *ws, size_t ws_bytes, long long nodes)
     return true;
 }
 
-// Fused P2M: the fast pass over all nodes (one kernel, or with node records the geometry and
-// solve kernels), then (quadratic shape functions, with a queue) the FP64 SVD pass over the
+// Fused P2M: the fast pass over all nodes (one kernel, or with node records and FP32 solves
+// the geometry and solve kernels), then (quadratic shape functions, with a queue) the FP64 SVD pass over the
 // nodes it queued.
 template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
 static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0, const NodeRecs *rec = nullptr)
@@ -118,7 +118,7 @@ static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0, const NodeRec
         if (e != cudaSuccess) return e;
     }
     cudaError_t e;
-    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && T == 0 && rec) {
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && T == 0 && rec && sizeof(S) == sizeof(float)) {
         k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *rec);
         count_launch();
         e = cudaGetLastError();

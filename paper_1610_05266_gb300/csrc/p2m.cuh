@@ -500,9 +500,9 @@ __global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
 }
 
 // ---------------------------------------------------------------- two-kernel fused P2M
-// The quadratic apply path as two kernels, so that the star search (large thread-private
-// state, latency bound) and the moment solves (register-heavy arithmetic) each get their own
-// register budget: k_p2m_geom locates the node and builds its particle set, k_p2m_solve
+// The quadratic apply path with FP32 solves as two kernels, so that the star search (large
+// thread-private state, latency bound) and the moment solves (register-heavy arithmetic) each
+// get their own register budget: k_p2m_geom locates the node and builds its particle set, k_p2m_solve
 // solves the three edge systems and applies the weights.  They hand over a per-node record,
 // one array per field so that both kernels access it coalesced.
 struct NodeRecs {
@@ -518,8 +518,12 @@ __host__ __device__ constexpr size_t node_recs_bytes_per_node()
     return sizeof(int) + 3 * sizeof(unsigned) + 3 * sizeof(double) + UMAX * sizeof(int);
 }
 
+// Resident 128-thread blocks per SM of the geometry kernel (sweep 12, 14, 16 on GB300: 14).
+#ifndef PFEM_GEOM_MIN_BLOCKS
+#define PFEM_GEOM_MIN_BLOCKS 14
+#endif
 template <typename P, typename V, typename R>
-__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
+__global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
@@ -573,8 +577,19 @@ __global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m_geom(P2MArgs a
     }
 }
 
+// Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
+// system without spills (sweep 8, 10, 12: 8); the FP64 residual of the refined solve needs 4.
+// (FP64 solves keep the single fused kernel, whose larger occupancy measured faster.)
+#ifndef PFEM_SOLVE_MIN_BLOCKS
+#define PFEM_SOLVE_MIN_BLOCKS 8
+#endif
+template <typename S, bool REFINE> constexpr int solve_min_blocks()
+{
+    return (sizeof(S) == 8 || REFINE) ? 4 : PFEM_SOLVE_MIN_BLOCKS;
+}
+
 template <typename P, typename V, typename R, typename S, bool REFINE>
-__global__ void __launch_bounds__(128, 8) k_p2m_solve(P2MArgs a, NodeRecs r)
+__global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solve(P2MArgs a, NodeRecs r)
 {
     const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (node >= r.nodes) return;
