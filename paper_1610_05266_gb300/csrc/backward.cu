@@ -31,6 +31,136 @@ struct BwdArgs {
 
 constexpr int KBWD = 32;   // distinct particles per node kept by the recompute kernel
 
+// The adjoint of one node over its particle set (us[0..nu), stencil masks vm, tri[e] = us[vi[e]]):
+// uw the weights, ub = gbar . alpha per particle, udx/udy the position adjoints (all zero on
+// entry).  Returns 0 or -PFEM_ERR_DEGENERATE (a moment matrix that cannot be factored).
+template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
+__device__ __forceinline__ int bwd_u_solve(const BwdArgs &b, const NodePos<P, R> &np, const R g[8],
+                                           const int tri[3], const int *us, int nu,
+                                           const unsigned vm[3], const int vi[3], R *uw, R *ub,
+                                           R *udx, R *udy)
+{
+    const P2MArgs &a = b.f;
+    int st = 0;
+    for (int i = 0; i < nu; ++i) {
+        R v[8];
+        load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
+        R t = R(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < a.C) t = fma(g[c], v[c], t);
+        ub[i] = t;
+    }
+    R d[3][2];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
+    const R Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
+    const R Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
+    const R Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
+    const R A2 = Na + Nb + Nc;
+    const R lam[3] = {Na / A2, Nb / A2, Nc / A2};
+    R lbar[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        uw[vi[e]] += lam[e];
+        lbar[e] = ub[vi[e]];
+    }
+    auto offset = [&](int i, S &x, S &y) {
+        R dx, dy;
+        np.off(a.pos, us[i], dx, dy);
+        x = S(dx);
+        y = S(dy);
+    };
+    if (SHAPE == PFEM_SHAPE_QUADRATIC)
+        for (int e = 0; e < 3 && st == 0; ++e) {
+            const int f = e == 2 ? 0 : e + 1;
+            const unsigned mask = vm[e] | vm[f];
+            const S rnx = S(d[e][0]), rny = S(d[e][1]), rsx = S(d[f][0]), rsy = S(d[f][1]);
+            const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
+            const S ex = rnx - rsx, ey = rny - rsy;
+            const S inv = S(1) / sqrt(ex * ex + ey * ey);
+            Moment<S> M;
+            M.zero();
+            S u[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int i = __ffs(m) - 1;
+                S ox, oy;
+                offset(i, ox, oy);
+                const S x = (ox - mx) * inv, y = (oy - my) * inv;
+                M.add(x, y);
+                const S bt = S(ub[i]);
+                const S p[6] = {S(1), x, y, x * x, x * y, y * y};
+#pragma unroll
+                for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
+            }
+            if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
+            const S tx = ex * inv, ty = ey * inv;
+            const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
+                             S(-0.5) * ty * ty};
+            S y[6], z[6];
+            M.solve(bb, y);
+            M.solve(u, z);
+            const S ce = S(2) * S(lam[e]) * S(lam[f]);
+            S Be = S(0);
+#pragma unroll
+            for (int r = 0; r < 6; ++r) Be = fma(u[r], y[r], Be);
+            lbar[e] += R(S(2) * S(lam[f]) * Be);
+            lbar[f] += R(S(2) * S(lam[e]) * Be);
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int i = __ffs(m) - 1;
+                S ox, oy;
+                offset(i, ox, oy);
+                const S x = (ox - mx) * inv, yy = (oy - my) * inv;
+                const S p[6] = {S(1), x, yy, x * x, x * yy, yy * yy};
+                S Am = S(0), Zm = S(0);
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+                    Am = fma(p[r], y[r], Am);
+                    Zm = fma(p[r], z[r], Zm);
+                }
+                uw[i] += R(ce * Am);
+                if (POS) {
+                    const S bt = S(ub[i]);
+                    S pb[6];
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) pb[r] = ce * ((bt - Zm) * y[r] - Am * z[r]);
+                    const S xb = pb[1] + S(2) * x * pb[3] + yy * pb[4];
+                    const S yb = pb[2] + x * pb[4] + S(2) * yy * pb[5];
+                    udx[i] += R(xb * inv);
+                    udy[i] += R(yb * inv);
+                }
+            }
+            if (POS) {
+                // b = [0,0,0,-tx^2/2,-tx ty/2,-ty^2/2], t = (r_nu - r_sg)/s
+                const S txb = ce * (-tx * z[3] - S(0.5) * ty * z[4]);
+                const S tyb = ce * (-S(0.5) * tx * z[4] - ty * z[5]);
+                udx[vi[e]] += R(txb * inv);
+                udy[vi[e]] += R(tyb * inv);
+                udx[vi[f]] -= R(txb * inv);
+                udy[vi[f]] -= R(tyb * inv);
+            }
+        }
+    if (POS && st == 0) {
+        // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
+        const R Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
+        const R nb0 = (lbar[0] - Lam) / A2, nb1 = (lbar[1] - Lam) / A2, nb2 = (lbar[2] - Lam) / A2;
+        // cross(u, v): d/du = (v.y, -v.x), d/dv = (-u.y, u.x)
+        R gx[3] = {R(0), R(0), R(0)}, gy[3] = {R(0), R(0), R(0)};
+        gx[1] += nb0 * d[2][1];  gy[1] -= nb0 * d[2][0];
+        gx[2] -= nb0 * d[1][1];  gy[2] += nb0 * d[1][0];
+        gx[2] += nb1 * d[0][1];  gy[2] -= nb1 * d[0][0];
+        gx[0] -= nb1 * d[2][1];  gy[0] += nb1 * d[2][0];
+        gx[0] += nb2 * d[1][1];  gy[0] -= nb2 * d[1][0];
+        gx[1] -= nb2 * d[0][1];  gy[1] += nb2 * d[0][0];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            udx[vi[e]] += gx[e];
+            udy[vi[e]] += gy[e];
+        }
+    }
+    return st;
+}
+
 template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
 __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
 {
@@ -91,124 +221,9 @@ __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
                     vm[e] = m;
                 }
             if (over) st = -PFEM_ERR_CAPACITY;
-            if (st == 0) {
-                for (int i = 0; i < nu; ++i) {
-                    R v[8];
-                    load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
-                    R t = R(0);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (c < a.C) t = fma(g[c], v[c], t);
-                    ub[i] = t;
-                }
-                R d[3][2];
-#pragma unroll
-                for (int e = 0; e < 3; ++e) np.off(a.pos, tri[e], d[e][0], d[e][1]);
-                const R Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
-                const R Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
-                const R Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
-                const R A2 = Na + Nb + Nc;
-                const R lam[3] = {Na / A2, Nb / A2, Nc / A2};
-                R lbar[3];
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    uw[vi[e]] += lam[e];
-                    lbar[e] = ub[vi[e]];
-                }
-                auto offset = [&](int i, S &x, S &y) {
-                    R dx, dy;
-                    np.off(a.pos, us[i], dx, dy);
-                    x = S(dx);
-                    y = S(dy);
-                };
-                if (SHAPE == PFEM_SHAPE_QUADRATIC)
-                    for (int e = 0; e < 3 && st == 0; ++e) {
-                        const int f = e == 2 ? 0 : e + 1;
-                        const unsigned mask = vm[e] | vm[f];
-                        const S rnx = S(d[e][0]), rny = S(d[e][1]), rsx = S(d[f][0]), rsy = S(d[f][1]);
-                        const S mx = (rnx + rsx) * S(0.5), my = (rny + rsy) * S(0.5);
-                        const S ex = rnx - rsx, ey = rny - rsy;
-                        const S inv = S(1) / sqrt(ex * ex + ey * ey);
-                        Moment<S> M;
-                        M.zero();
-                        S u[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-                        for (unsigned m = mask; m; m &= m - 1) {
-                            const int i = __ffs(m) - 1;
-                            S ox, oy;
-                            offset(i, ox, oy);
-                            const S x = (ox - mx) * inv, y = (oy - my) * inv;
-                            M.add(x, y);
-                            const S bt = S(ub[i]);
-                            const S p[6] = {S(1), x, y, x * x, x * y, y * y};
-#pragma unroll
-                            for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
-                        }
-                        if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
-                        const S tx = ex * inv, ty = ey * inv;
-                        const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
-                                         S(-0.5) * ty * ty};
-                        S y[6], z[6];
-                        M.solve(bb, y);
-                        M.solve(u, z);
-                        const S ce = S(2) * S(lam[e]) * S(lam[f]);
-                        S Be = S(0);
-#pragma unroll
-                        for (int r = 0; r < 6; ++r) Be = fma(u[r], y[r], Be);
-                        lbar[e] += R(S(2) * S(lam[f]) * Be);
-                        lbar[f] += R(S(2) * S(lam[e]) * Be);
-                        for (unsigned m = mask; m; m &= m - 1) {
-                            const int i = __ffs(m) - 1;
-                            S ox, oy;
-                            offset(i, ox, oy);
-                            const S x = (ox - mx) * inv, yy = (oy - my) * inv;
-                            const S p[6] = {S(1), x, yy, x * x, x * yy, yy * yy};
-                            S Am = S(0), Zm = S(0);
-#pragma unroll
-                            for (int r = 0; r < 6; ++r) {
-                                Am = fma(p[r], y[r], Am);
-                                Zm = fma(p[r], z[r], Zm);
-                            }
-                            uw[i] += R(ce * Am);
-                            if (POS) {
-                                const S bt = S(ub[i]);
-                                S pb[6];
-#pragma unroll
-                                for (int r = 0; r < 6; ++r) pb[r] = ce * ((bt - Zm) * y[r] - Am * z[r]);
-                                const S xb = pb[1] + S(2) * x * pb[3] + yy * pb[4];
-                                const S yb = pb[2] + x * pb[4] + S(2) * yy * pb[5];
-                                udx[i] += R(xb * inv);
-                                udy[i] += R(yb * inv);
-                            }
-                        }
-                        if (POS) {
-                            // b = [0,0,0,-tx^2/2,-tx ty/2,-ty^2/2], t = (r_nu - r_sg)/s
-                            const S txb = ce * (-tx * z[3] - S(0.5) * ty * z[4]);
-                            const S tyb = ce * (-S(0.5) * tx * z[4] - ty * z[5]);
-                            udx[vi[e]] += R(txb * inv);
-                            udy[vi[e]] += R(tyb * inv);
-                            udx[vi[f]] -= R(txb * inv);
-                            udy[vi[f]] -= R(tyb * inv);
-                        }
-                    }
-                if (POS && st == 0) {
-                    // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
-                    const R Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
-                    const R nb0 = (lbar[0] - Lam) / A2, nb1 = (lbar[1] - Lam) / A2, nb2 = (lbar[2] - Lam) / A2;
-                    // cross(u, v): d/du = (v.y, -v.x), d/dv = (-u.y, u.x)
-                    R gx[3] = {R(0), R(0), R(0)}, gy[3] = {R(0), R(0), R(0)};
-                    gx[1] += nb0 * d[2][1];  gy[1] -= nb0 * d[2][0];
-                    gx[2] -= nb0 * d[1][1];  gy[2] += nb0 * d[1][0];
-                    gx[2] += nb1 * d[0][1];  gy[2] -= nb1 * d[0][0];
-                    gx[0] -= nb1 * d[2][1];  gy[0] += nb1 * d[2][0];
-                    gx[0] += nb2 * d[1][1];  gy[0] -= nb2 * d[1][0];
-                    gx[1] -= nb2 * d[0][1];  gy[1] += nb2 * d[0][0];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        udx[vi[e]] += gx[e];
-                        udy[vi[e]] += gy[e];
-                    }
-                }
-            }
+            if (st == 0)
+                st = bwd_u_solve<P, V, R, S, SHAPE, POS>(b, np, g, tri, us, nu, vm, vi, uw, ub,
+                                                         udx, udy);
         }
         if (st != 0) {
             record_error(a.status, -st, node);
@@ -233,6 +248,70 @@ __global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_bwd_node(BwdArgs b
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
     if (I >= b.f.n || J >= b.f.n) return;
     bwd_node<P, V, R, S, SHAPE, POS>(b, I, J);
+}
+
+// The adjoint with FP32 solves as two kernels, as in the forward: k_p2m_geom writes each
+// node's record (particle set, stencil masks), this kernel solves the adjoint of the three edge
+// systems with its own register budget and writes the node's entries.
+template <typename P, typename V, typename R, typename S, bool POS>
+__global__ void __launch_bounds__(128, 4) k_bwd_solve(BwdArgs b, NodeRecs r)
+{
+    const P2MArgs &a = b.f;
+    const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (node >= r.nodes) return;
+    int *oslot = b.e_slot + node * b.K;
+    R *ow = (R *)b.e_w + node * b.K;
+    R *od = POS ? (R *)b.e_dpos + node * b.K * 2 : nullptr;
+    R g[8];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        g[c] = c < a.C ? load_val<V, R>((const V *)b.grad_mesh + node * a.C + c) : R(0);
+        any |= g[c] != R(0);
+    }
+    int us[UMAX];
+    R uw[UMAX], ub[UMAX], udx[UMAX], udy[UMAX];
+    int nu = 0;
+    const int meta = r.meta[node];
+    if (any && meta >= 0) {
+        nu = meta & 31;
+        const int vi[3] = {(meta >> 5) & 31, (meta >> 10) & 31, (meta >> 15) & 31};
+        if (nu > b.K) {
+            record_error(a.status, PFEM_ERR_CAPACITY, node);
+            nu = 0;
+        } else {
+            for (int i = 0; i < nu; ++i) {
+                us[i] = r.us[i * r.nodes + node];
+                uw[i] = udx[i] = udy[i] = R(0);
+            }
+            unsigned vm[3];
+            int tri[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                vm[e] = r.mask[e * r.nodes + node];
+                tri[e] = us[vi[e]];
+            }
+            const int nc = a.n - 1;
+            const int I = (int)(node % a.n), J = (int)(node / a.n);
+            NodePos<P, R> np;
+            np.init(I == nc ? 0 : I, J == nc ? 0 : J, nc);
+            const int st = bwd_u_solve<P, V, R, S, PFEM_SHAPE_QUADRATIC, POS>(
+                b, np, g, tri, us, nu, vm, vi, uw, ub, udx, udy);
+            if (st != 0) {
+                record_error(a.status, -st, node);
+                nu = 0;
+            }
+        }
+    }
+    for (int k = 0; k < b.K; ++k) {
+        const bool v = k < nu;
+        oslot[k] = v ? us[k] : -1;
+        ow[k] = v ? uw[k] : R(0);
+        if (POS) {
+            od[2 * k] = v ? udx[k] : R(0);
+            od[2 * k + 1] = v ? udy[k] : R(0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- transposed gather
@@ -335,6 +414,8 @@ BwdLayout bwd_layout(int n, long long N, int Kw)
     L.rank = off;    off = al(off + 4 * (size_t)E);
     L.order = off;   off = al(off + 4 * (size_t)E);
     L.scan = off;    off = al(off + 4 * scan_scratch_ints(N + 1));
+    NodeRecs r;
+    L.rec = off;     off = al(off + node_recs_layout(nullptr, (long long)n * n, &r));
     L.total = off;
     return L;
 }
@@ -396,25 +477,37 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
     b.e_w = ws + L.e_w;
     b.e_dpos = ws + L.e_dpos;
     const dim3 grid((g.n + 15) / 16, (g.n + 7) / 8);
+    // per-node adjoint entries: the geometry and solve kernels for FP32 quadratic solves, else
+    // the single fused kernel
+    NodeRecs recs;
+    node_recs_layout(ws + L.rec, (long long)g.n * g.n, &recs);
+    const bool split = SHAPE == PFEM_SHAPE_QUADRATIC && sizeof(S) == sizeof(float);
+    auto node_pass = [&](bool pos) {
+        if (split) {
+            k_p2m_geom<P, V, R><<<grid, 128, 0, s>>>(b.f, recs);
+            const unsigned blocks = (unsigned)((recs.nodes + 127) / 128);
+            if (pos) k_bwd_solve<P, V, R, S, true><<<blocks, 128, 0, s>>>(b, recs);
+            else k_bwd_solve<P, V, R, S, false><<<blocks, 128, 0, s>>>(b, recs);
+            count_launch(2);
+        } else {
+            if (pos) k_bwd_node<P, V, R, S, SHAPE, true><<<grid, 128, 0, s>>>(b);
+            else k_bwd_node<P, V, R, S, SHAPE, false><<<grid, 128, 0, s>>>(b);
+            count_launch();
+        }
+    };
     if (checkpoint) {
         // value gradient straight from the stored weights
         cudaError_t e = transposed_gather<V, R, R>(g.n, g.N, Kw, C, w_idx, (const R *)w,
                                                    (const R *)nullptr, grad_mesh, perm, grad_vals,
                                                    nullptr, L, ws, s);
         if (e != cudaSuccess || !grad_pos) return e;
-        k_bwd_node<P, V, R, S, SHAPE, true><<<grid, 128, 0, s>>>(b);
-        count_launch();
+        node_pass(true);
         return transposed_gather<V, R, R>(g.n, g.N, K, C, b.e_slot, (const R *)b.e_w,
                                           (const R *)b.e_dpos, grad_mesh, perm, nullptr, grad_pos,
                                           L, ws, s);
     }
-    if (grad_pos) {
-        k_bwd_node<P, V, R, S, SHAPE, true><<<grid, 128, 0, s>>>(b);
-    } else {
-        b.e_dpos = nullptr;
-        k_bwd_node<P, V, R, S, SHAPE, false><<<grid, 128, 0, s>>>(b);
-    }
-    count_launch();
+    if (!grad_pos) b.e_dpos = nullptr;
+    node_pass(grad_pos != nullptr);
     return transposed_gather<V, R, R>(g.n, g.N, K, C, b.e_slot, (const R *)b.e_w,
                                       grad_pos ? (const R *)b.e_dpos : nullptr, grad_mesh, perm,
                                       grad_vals, grad_pos, L, ws, s);

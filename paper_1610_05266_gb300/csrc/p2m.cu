@@ -83,26 +83,14 @@ static size_t recs_offset(long long nodes) { return al256(512 + 8 * (size_t)node
 
 size_t p2m_ws_bytes(long long nodes)
 {
-    size_t off = recs_offset(nodes);
-    off = al256(off + sizeof(int) * (size_t)nodes);
-    off = al256(off + 3 * sizeof(unsigned) * (size_t)nodes);
-    off = al256(off + 3 * sizeof(double) * (size_t)nodes);
-    return off + UMAX * sizeof(int) * (size_t)nodes;
+    NodeRecs r;
+    return recs_offset(nodes) + node_recs_layout(nullptr, nodes, &r);
 }
 
 static bool set_recs(NodeRecs &r, void *ws, size_t ws_bytes, long long nodes)
 {
     if (ws_bytes < p2m_ws_bytes(nodes)) return false;
-    char *b = (char *)ws;
-    size_t off = recs_offset(nodes);
-    r.meta = (int *)(b + off);
-    off = al256(off + sizeof(int) * (size_t)nodes);
-    r.mask = (unsigned *)(b + off);
-    off = al256(off + 3 * sizeof(unsigned) * (size_t)nodes);
-    r.lam = (double *)(b + off);
-    off = al256(off + 3 * sizeof(double) * (size_t)nodes);
-    r.us = (int *)(b + off);
-    r.nodes = nodes;
+    node_recs_layout((char *)ws + recs_offset(nodes), nodes, &r);
     return true;
 }
 

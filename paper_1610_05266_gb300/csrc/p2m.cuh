@@ -513,9 +513,24 @@ struct NodeRecs {
     long long nodes;
 };
 
-__host__ __device__ constexpr size_t node_recs_bytes_per_node()
+// Lays the record arrays for `nodes` nodes out from `base` (256-byte aligned arrays; base may be
+// null to size them); returns the bytes they take.
+inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r)
 {
-    return sizeof(int) + 3 * sizeof(unsigned) + 3 * sizeof(double) + UMAX * sizeof(int);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_meta = 0;
+    const size_t o_mask = al(o_meta + sizeof(int) * (size_t)nodes);
+    const size_t o_lam = al(o_mask + 3 * sizeof(unsigned) * (size_t)nodes);
+    const size_t o_us = al(o_lam + 3 * sizeof(double) * (size_t)nodes);
+    const size_t total = al(o_us + UMAX * sizeof(int) * (size_t)nodes);
+    if (base) {
+        r->meta = (int *)(base + o_meta);
+        r->mask = (unsigned *)(base + o_mask);
+        r->lam = (double *)(base + o_lam);
+        r->us = (int *)(base + o_us);
+    }
+    r->nodes = nodes;
+    return total;
 }
 
 // Resident 128-thread blocks per SM of the geometry kernel (sweep 12, 14, 16 on GB300: 14).
@@ -555,7 +570,7 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
         int vi[3];
         const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
         if (node_u_build<UMAX>(tri, sa, lam, us, uw, nu, vm, vi) != 0) {
-            st = -PFEM_DEFER;
+            st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
         } else {
             for (int i = 0; i < nu; ++i) r.us[i * r.nodes + node] = us[i];
 #pragma unroll
@@ -570,10 +585,12 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
     if (st != 0) {
         st = defer_or_error(a, st, node);
         if (st < 0) record_error(a.status, -st, node);
-        R acc[8];
+        if (a.out) {                    // the adjoint uses this kernel without a mesh output
+            R acc[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
-        store_vals<V, R>((V *)a.out, node, a.C, acc);
+            for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+            store_vals<V, R>((V *)a.out, node, a.C, acc);
+        }
     }
 }
 
