@@ -253,8 +253,9 @@ size_t pfem_batch_plan_size(int32_t P);
 pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, void *plan,
                                  int64_t *totals);
 
-/* Workspace bytes of pfem_batch_build_cells / pfem_batch_project_p2m. */
-size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total);
+/* Workspace bytes of pfem_batch_build_cells / pfem_batch_project_p2m for the totals of
+ * pfem_batch_plan_init (nodes_total = 0: binning only). */
+size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total, int64_t nodes_total);
 
 /* Binning of every problem at once (a1-a2 on the concatenated layout). */
 pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bins_total,
@@ -264,8 +265,14 @@ pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bi
 
 /* P2M of every problem in one persistent launch: `blocks` blocks of 16 x tile_rows threads
  * (tile_rows 4, 8 or 16) pull (problem, 16 x tile_rows node tile) items from a counter in ws.
- * Values FP32 (FP32 positions) or FP64 (FP64 positions, FP64 solve). */
-pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfem_dtype pos_t,
+ * Values FP32 (FP32 positions) or FP64 (FP64 positions, FP64 solve).  Quadratic shape
+ * functions with FP32 solves run as two launches when ws holds the per-node records
+ * (pfem_batch_workspace_size with nodes_total, the plan's total nodes): the persistent kernel
+ * writes each node's particle set and a second kernel solves its edge systems.  There is no
+ * SVD pass here: a node whose moment system the Cholesky solve cannot factor records
+ * PFEM_ERR_DEGENERATE. */
+pfem_status pfem_batch_project_p2m(const void *plan, int64_t nodes_total, const void *pos_sorted,
+                                   pfem_dtype pos_t,
                                    const uint32_t *q_sorted, const int32_t *cell_start,
                                    const int32_t *perm, int32_t C, const void *vals,
                                    pfem_dtype val_t, pfem_shape shape, pfem_solve solve,

@@ -55,10 +55,10 @@ SIGNATURES = {
                                                 _p, _p, ctypes.c_int, _p, _p, _p]),
     "pfem_batch_plan_size": (_sz, [_i32]),
     "pfem_batch_plan_init": (ctypes.c_int, [_i32, _p, _p, ctypes.POINTER(_i64)]),
-    "pfem_batch_workspace_size": (_sz, [_i64, _i64]),
+    "pfem_batch_workspace_size": (_sz, [_i64, _i64, _i64]),
     "pfem_batch_build_cells": (ctypes.c_int, [_p, _i64, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p,
                                               _sz, _p]),
-    "pfem_batch_project_p2m": (ctypes.c_int, [_p, _p, ctypes.c_int, _p, _p, _p, _i32, _p,
+    "pfem_batch_project_p2m": (ctypes.c_int, [_p, _i64, _p, ctypes.c_int, _p, _p, _p, _i32, _p,
                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _i32,
                                               _i32, _p, _sz, _p]),
     "pfem_batch_interp_m2p": (ctypes.c_int, [_p, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int, _i32,

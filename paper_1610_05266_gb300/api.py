@@ -134,8 +134,8 @@ def pfem_batch_plan_init(problems, plan: torch.Tensor):
     return int(tot[0]), int(tot[1]), int(tot[2])
 
 
-def pfem_batch_workspace_size(N_total: int, bins_total: int) -> int:
-    return int(L.load().pfem_batch_workspace_size(N_total, bins_total))
+def pfem_batch_workspace_size(N_total: int, bins_total: int, nodes_total: int = 0) -> int:
+    return int(L.load().pfem_batch_workspace_size(N_total, bins_total, nodes_total))
 
 
 def pfem_batch_build_cells(plan, N_total, bins_total, pos, cell_start, perm, pos_sorted, q_sorted,
@@ -147,9 +147,10 @@ def pfem_batch_build_cells(plan, N_total, bins_total, pos, cell_start, perm, pos
           "pfem_batch_build_cells")
 
 
-def pfem_batch_project_p2m(plan, pos_sorted, q_sorted, cell_start, perm, C, vals, shape, solve,
-                           mesh_vals, tile_rows, blocks, ws, stream=None):
-    check(L.load().pfem_batch_project_p2m(ptr(plan), ptr(pos_sorted), dtype_code(pos_sorted.dtype),
+def pfem_batch_project_p2m(plan, nodes_total, pos_sorted, q_sorted, cell_start, perm, C, vals,
+                           shape, solve, mesh_vals, tile_rows, blocks, ws, stream=None):
+    check(L.load().pfem_batch_project_p2m(ptr(plan), nodes_total, ptr(pos_sorted),
+                                          dtype_code(pos_sorted.dtype),
                                           ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
                                           dtype_code(vals.dtype), shape, solve, ptr(mesh_vals),
                                           tile_rows, blocks, ptr(ws), ws.numel() * ws.element_size(),
@@ -321,7 +322,7 @@ class Batch:
         self.perm = torch.empty(self.N_total, dtype=torch.int32, device=dev)
         self.pos_sorted = torch.empty((self.N_total, 2), dtype=dtype, device=dev)
         self.q_sorted = torch.empty((self.N_total, 2), dtype=torch.int32, device=dev)
-        wsb = pfem_batch_workspace_size(self.N_total, self.bins_total)
+        wsb = pfem_batch_workspace_size(self.N_total, self.bins_total, self.nodes_total)
         self.ws = torch.zeros((wsb + 7) // 8, dtype=torch.float64, device=dev)
         self.mesh = torch.empty((self.nodes_total, C), dtype=dtype, device=dev)
         self.back = torch.empty((self.N_total, C), dtype=dtype, device=dev)
@@ -345,7 +346,7 @@ class Batch:
             stream=None):
         if solve is None:
             solve = PFEM_SOLVE_F64 if vals.dtype == torch.float64 else PFEM_SOLVE_F32
-        pfem_batch_project_p2m(self.plan, self.pos_sorted, self.q_sorted, self.cell_start,
+        pfem_batch_project_p2m(self.plan, self.nodes_total, self.pos_sorted, self.q_sorted, self.cell_start,
                                self.perm, self.C, vals, shape, solve, self.mesh,
                                tile_rows or self.config["tile_rows"],
                                blocks or self.config["p2m_blocks"], self.ws, stream)

@@ -131,6 +131,42 @@ __global__ void __launch_bounds__(256, PFEM_P2M_MIN_BLOCKS / 2) k_p2m_batch(cons
     }
 }
 
+// The quadratic P2M with FP32 solves in two kernels, as for one problem: this persistent kernel
+// writes every node's record (at its problem's node offset, with its coordinates), then
+// k_p2m_solve runs over all nodes of the batch.
+template <typename P, typename V, typename R>
+__global__ void __launch_bounds__(256, PFEM_GEOM_MIN_BLOCKS / 2) k_p2m_batch_geom(
+    const BPlanDev *pl, int shape_idx, P2MArgs base, unsigned long long *counter, NodeRecs r)
+{
+    __shared__ long long item;
+    const int TY = blockDim.x / 16;
+    const long long total = pl->n_items[shape_idx];
+    const long long *tp = plan_tiles(pl, shape_idx);
+    for (int guard = 0; guard < (1 << 30); ++guard) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = item;
+        if (it >= total) break;
+        const int p = find_item(tp, pl->P, it);
+        const BDesc d = plan_desc(pl)[p];
+        const long long t = it - tp[p];
+        const int tiles_x = (d.n + 15) / 16;
+        const int I = (int)(t % tiles_x) * 16 + (threadIdx.x & 15);
+        const int J = (int)(t / tiles_x) * TY + (threadIdx.x >> 4);
+        if (I >= d.n || J >= d.n) continue;
+        P2MArgs a = base;
+        a.n = d.n;
+        a.B.start = base.B.start + d.boff;
+        a.B.nb = d.nb;
+        a.B.rmax = d.rmax;
+        a.B.dmax = d.dmax;
+        a.R0 = d.R0;
+        a.out = (void *)((V *)base.out + d.noff * base.C);
+        geom_node<P, V, R>(a, r, I, J, d.noff + (long long)J * d.n + I);
+    }
+}
+
 // ---------------------------------------------------------------- M2P
 
 template <typename P, typename V, typename R>
@@ -244,22 +280,44 @@ cudaError_t launch_batch_build_cells(const void *plan, long long Ntot, long long
 
 template <typename P, typename V, typename R, typename S, bool REF, int SHAPE>
 static cudaError_t p2m_batch_t(const void *plan, const P2MArgs &base, int shape_idx, int blocks,
-                               unsigned long long *counter, cudaStream_t s)
+                               unsigned long long *counter, const NodeRecs *rec, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int TYs[BT_SHAPES] = {4, 8, 16};
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && sizeof(S) == sizeof(float) && rec) {
+        k_p2m_batch_geom<P, V, R><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
+            (const BPlanDev *)plan, shape_idx, base, counter, *rec);
+        k_p2m_solve<P, V, R, S, REF><<<(unsigned)((rec->nodes + 127) / 128), 128, 0, s>>>(base, *rec);
+        count_launch(2);
+        return cudaGetLastError();
+    }
     k_p2m_batch<P, V, R, S, REF, SHAPE><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
         (const BPlanDev *)plan, shape_idx, base, counter);
     count_launch();
     return cudaGetLastError();
 }
 
+// Workspace of the batched P2M: status (byte 0) and work counter (byte 64), then the node
+// records of the two-kernel path from byte 256.
+size_t batch_p2m_ws_bytes(long long nodes_total)
+{
+    NodeRecs r;
+    return 256 + node_recs_layout(nullptr, nodes_total, &r, true);
+}
+
 cudaError_t launch_batch_p2m(const void *plan, const void *pos_sorted, const uint32_t *q_sorted,
                              const int *cell_start, const int *perm, int C, const void *vals,
                              pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *mesh,
-                             int shape_idx, int blocks, void *ws, cudaStream_t s)
+                             int shape_idx, int blocks, long long nodes_total, void *ws,
+                             size_t ws_bytes, cudaStream_t s)
 {
+    NodeRecs recs;
+    const NodeRecs *rec = nullptr;
+    if (nodes_total > 0 && ws_bytes >= batch_p2m_ws_bytes(nodes_total)) {
+        node_recs_layout((char *)ws + 256, nodes_total, &recs, true);
+        rec = &recs;
+    }
     P2MArgs a;
     a.n = 0;
     a.B.q = (const uint2 *)q_sorted;
@@ -280,14 +338,14 @@ cudaError_t launch_batch_p2m(const void *plan, const void *pos_sorted, const uin
     unsigned long long *counter = (unsigned long long *)((char *)ws + 64);
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
     if (val_t == PFEM_F64) {
-        if (!q) return p2m_batch_t<double, double, double, double, false, 0>(plan, a, shape_idx, blocks, counter, s);
-        return p2m_batch_t<double, double, double, double, false, 1>(plan, a, shape_idx, blocks, counter, s);
+        if (!q) return p2m_batch_t<double, double, double, double, false, 0>(plan, a, shape_idx, blocks, counter, rec, s);
+        return p2m_batch_t<double, double, double, double, false, 1>(plan, a, shape_idx, blocks, counter, rec, s);
     }
     if (val_t == PFEM_F32) {
-        if (!q) return p2m_batch_t<float, float, float, float, false, 0>(plan, a, shape_idx, blocks, counter, s);
-        if (solve == PFEM_SOLVE_F64) return p2m_batch_t<float, float, float, double, false, 1>(plan, a, shape_idx, blocks, counter, s);
-        if (solve == PFEM_SOLVE_F32) return p2m_batch_t<float, float, float, float, false, 1>(plan, a, shape_idx, blocks, counter, s);
-        return p2m_batch_t<float, float, float, float, true, 1>(plan, a, shape_idx, blocks, counter, s);
+        if (!q) return p2m_batch_t<float, float, float, float, false, 0>(plan, a, shape_idx, blocks, counter, rec, s);
+        if (solve == PFEM_SOLVE_F64) return p2m_batch_t<float, float, float, double, false, 1>(plan, a, shape_idx, blocks, counter, rec, s);
+        if (solve == PFEM_SOLVE_F32) return p2m_batch_t<float, float, float, float, false, 1>(plan, a, shape_idx, blocks, counter, rec, s);
+        return p2m_batch_t<float, float, float, float, true, 1>(plan, a, shape_idx, blocks, counter, rec, s);
     }
     return cudaErrorInvalidValue;
 }

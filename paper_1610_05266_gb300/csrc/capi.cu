@@ -330,10 +330,11 @@ pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, 
     return PFEM_OK;
 }
 
-size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total)
+size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total, int64_t nodes_total)
 {
-    if (N_total < 0 || bins_total < 1) return 0;
-    return ws_layout_bins(bins_total, N_total).total;
+    if (N_total < 0 || bins_total < 1 || nodes_total < 0) return 0;
+    const size_t b = ws_layout_bins(bins_total, N_total).total;
+    return nodes_total > 0 ? std::max(b, batch_p2m_ws_bytes(nodes_total)) : b;
 }
 
 pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bins_total,
@@ -350,7 +351,8 @@ pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bi
                                               pos_sorted, q_sorted, L, ws, (cudaStream_t)stream));
 }
 
-pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfem_dtype pos_t,
+pfem_status pfem_batch_project_p2m(const void *plan, int64_t nodes_total, const void *pos_sorted,
+                                   pfem_dtype pos_t,
                                    const uint32_t *q_sorted, const int32_t *cell_start,
                                    const int32_t *perm, int32_t C, const void *vals,
                                    pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
@@ -359,7 +361,7 @@ pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfe
 {
     if (!plan || !pos_sorted || !q_sorted || !cell_start || !perm || !vals || !mesh_vals || !ws)
         return PFEM_ERR_INVALID_ARG;
-    if (C < 1 || C > 8 || blocks < 1 || ws_bytes < 256) return PFEM_ERR_INVALID_ARG;
+    if (C < 1 || C > 8 || blocks < 1 || ws_bytes < 256 || nodes_total < 0) return PFEM_ERR_INVALID_ARG;
     const int sidx = tile_rows == 4 ? 0 : tile_rows == 8 ? 1 : tile_rows == 16 ? 2 : -1;
     if (sidx < 0) return PFEM_ERR_INVALID_ARG;
     if (shape != PFEM_SHAPE_LINEAR && shape != PFEM_SHAPE_QUADRATIC) return PFEM_ERR_INVALID_ARG;
@@ -368,7 +370,8 @@ pfem_status pfem_batch_project_p2m(const void *plan, const void *pos_sorted, pfe
     if (val_t == PFEM_BF16) return PFEM_ERR_INVALID_ARG;
     if (solve < PFEM_SOLVE_F64 || solve > PFEM_SOLVE_F32_REFINED) return PFEM_ERR_INVALID_ARG;
     return from_cuda(launch_batch_p2m(plan, pos_sorted, q_sorted, cell_start, perm, C, vals, val_t,
-                                      shape, solve, mesh_vals, sidx, blocks, ws, (cudaStream_t)stream));
+                                      shape, solve, mesh_vals, sidx, blocks, nodes_total, ws,
+                                      ws_bytes, (cudaStream_t)stream));
 }
 
 pfem_status pfem_batch_interp_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int32_t C,

@@ -33,7 +33,9 @@ cudaError_t launch_batch_build_cells(const void *plan, long long Ntot, long long
 cudaError_t launch_batch_p2m(const void *plan, const void *pos_sorted, const uint32_t *q_sorted,
                              const int *cell_start, const int *perm, int C, const void *vals,
                              pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *mesh,
-                             int shape_idx, int blocks, void *ws, cudaStream_t s);
+                             int shape_idx, int blocks, long long nodes_total, void *ws,
+                             size_t ws_bytes, cudaStream_t s);
+size_t batch_p2m_ws_bytes(long long nodes_total);
 cudaError_t launch_batch_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int C,
                              const void *mesh, void *vals, pfem_dtype val_t, int blocks,
                              cudaStream_t s);

@@ -510,24 +510,27 @@ struct NodeRecs {
     unsigned *mask;     // [3][nodes] vm[e]
     double *lam;        // [3][nodes] barycentric coordinates (exact in both precisions)
     int *us;            // [UMAX][nodes] slots of the particle set
+    long long *loc;     // [nodes] Iu | Ju << 21 | nc << 42 (batches of problems), or null
     long long nodes;
 };
 
 // Lays the record arrays for `nodes` nodes out from `base` (256-byte aligned arrays; base may be
 // null to size them); returns the bytes they take.
-inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r)
+inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r, bool with_loc = false)
 {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t o_meta = 0;
     const size_t o_mask = al(o_meta + sizeof(int) * (size_t)nodes);
     const size_t o_lam = al(o_mask + 3 * sizeof(unsigned) * (size_t)nodes);
     const size_t o_us = al(o_lam + 3 * sizeof(double) * (size_t)nodes);
-    const size_t total = al(o_us + UMAX * sizeof(int) * (size_t)nodes);
+    const size_t o_loc = al(o_us + UMAX * sizeof(int) * (size_t)nodes);
+    const size_t total = with_loc ? al(o_loc + sizeof(long long) * (size_t)nodes) : o_loc;
     if (base) {
         r->meta = (int *)(base + o_meta);
         r->mask = (unsigned *)(base + o_mask);
         r->lam = (double *)(base + o_lam);
         r->us = (int *)(base + o_us);
+        r->loc = with_loc ? (long long *)(base + o_loc) : nullptr;
     }
     r->nodes = nodes;
     return total;
@@ -537,12 +540,13 @@ inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r)
 #ifndef PFEM_GEOM_MIN_BLOCKS
 #define PFEM_GEOM_MIN_BLOCKS 14
 #endif
+// Node (I, J) of the mesh of a.n nodes per side: locate it, build its particle set and write
+// its record at index `rec` (node J * a.n + I of a single problem; the problem's offset plus
+// that in a batch, which also records the node's coordinates).
 template <typename P, typename V, typename R>
-__global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
+__device__ __forceinline__ void geom_node(const P2MArgs &a, const NodeRecs &r, int I, int J,
+                                          long long rec)
 {
-    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
-    if (I >= a.n || J >= a.n) return;
     const int nc = a.n - 1;
     const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
     const long long node = (long long)J * a.n + I;
@@ -572,16 +576,17 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
         if (node_u_build<UMAX>(tri, sa, lam, us, uw, nu, vm, vi) != 0) {
             st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
         } else {
-            for (int i = 0; i < nu; ++i) r.us[i * r.nodes + node] = us[i];
+            for (int i = 0; i < nu; ++i) r.us[i * r.nodes + rec] = us[i];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                r.mask[e * r.nodes + node] = vm[e];
-                r.lam[e * r.nodes + node] = (double)lam[e];
+                r.mask[e * r.nodes + rec] = vm[e];
+                r.lam[e * r.nodes + rec] = (double)lam[e];
             }
             meta = nu | vi[0] << 5 | vi[1] << 10 | vi[2] << 15;
         }
     }
-    r.meta[node] = meta;
+    r.meta[rec] = meta;
+    if (r.loc) r.loc[rec] = (long long)Iu | (long long)Ju << 21 | (long long)nc << 42;
     if (st != 0) {
         st = defer_or_error(a, st, node);
         if (st < 0) record_error(a.status, -st, node);
@@ -592,6 +597,15 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
             store_vals<V, R>((V *)a.out, node, a.C, acc);
         }
     }
+}
+
+template <typename P, typename V, typename R>
+__global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
+    geom_node<P, V, R>(a, r, I, J, (long long)J * a.n + I);
 }
 
 // Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
@@ -628,10 +642,15 @@ __global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solv
         lam[e] = (R)r.lam[e * r.nodes + node];
         uw[vi[e]] += lam[e];
     }
-    const int nc = a.n - 1;
-    const int I = (int)(node % a.n), J = (int)(node / a.n);
     NodePos<P, R> np;
-    np.init(I == nc ? 0 : I, J == nc ? 0 : J, nc);
+    if (r.loc) {                        // batch: the node's own mesh, output at its record index
+        const long long l = r.loc[node];
+        np.init((int)(l & 0x1fffff), (int)((l >> 21) & 0x1fffff), (int)(l >> 42));
+    } else {
+        const int nc = a.n - 1;
+        const int I = (int)(node % a.n), J = (int)(node / a.n);
+        np.init(I == nc ? 0 : I, J == nc ? 0 : J, nc);
+    }
     int st = node_u_solve<P, R, S, REFINE, false, UMAX>(a, np, us, uw, vm, vi, lam);
     R acc[8];
 #pragma unroll
