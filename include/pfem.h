@@ -164,10 +164,12 @@ pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *p
  * fast tolerance (rank deficient, e.g. a stencil of five particles, or too ill-conditioned for
  * the precision: 3e-4 of the trace in FP32, 1e-6 in FP64), or with more than 24 distinct
  * particles, is queued and recomputed in FP64 with the minimum-norm least-squares solution by
- * SVD (App. A), by a second kernel on the same stream.  The queue uses the workspace after
+ * SVD (App. A), by a further kernel on the same stream.  The queue uses the workspace after
  * its first 512 bytes (8 bytes per queued node, at most n*n): with ws_bytes < 520 there is no
  * queue and such nodes record PFEM_ERR_DEGENERATE (PFEM_ERR_CAPACITY when the queue is full).
- * The workspace of pfem_workspace_size() leaves room for every node. */
+ * With FP32 solves and room after the queue for 136 bytes of record per node, the fast pass
+ * runs as a geometry kernel and a solve kernel handing over those records; with less, as one
+ * fused kernel (same results).  The workspace of pfem_workspace_size() has room for both. */
 pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                              pfem_dtype pos_t, const uint32_t *q_sorted,
                              const int32_t *cell_start, const int32_t *perm, int32_t C,
