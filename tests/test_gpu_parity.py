@@ -418,3 +418,25 @@ def test_ill_conditioned_nodes_take_the_svd_pass(P):
     proj.check("weights")
     mesh_w = proj.p2m(v, weights=(w_idx, w))
     assert np.abs(mesh_w.cpu().numpy().astype(np.float64) - ref).max() <= 1e-5 * vmax
+
+
+@pytest.mark.parametrize("solve", ["f32", "f32ref"])
+def test_fused_and_split_fast_pass_agree(P, solve):
+    """With a workspace of 512 bytes (status only: no queue, no node records) the quadratic
+    P2M runs its fast pass as one fused kernel; with the full workspace, as the geometry and
+    solve kernels.  Same arithmetic in the same order: bit-identical meshes, no device error."""
+    from paper_1610_05266_gb300 import api
+    sv = {"f32": P.PFEM_SOLVE_F32, "f32ref": P.PFEM_SOLVE_F32_REFINED}[solve]
+    pr = G.scaled_config("tgz", 129, 256)
+    proj, _ = gpu_setup(P, pr, torch.float32)
+    v = torch.tensor(pr.vals, dtype=torch.float32, device="cuda")
+    split = proj.p2m(v, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv)
+    proj.check("split")
+    c = proj.cells
+    small = torch.zeros(64, dtype=torch.float64, device="cuda")
+    fused = torch.empty_like(split)
+    api.pfem_project_p2m(pr.n, proj.nb, pr.N, c.pos_sorted, c.q_sorted, c.cell_start, c.perm,
+                         pr.C, v, P.PFEM_SHAPE_QUADRATIC, sv, None, None, 0, fused, small)
+    code, _ = api.pfem_read_status(small)
+    assert code == 0
+    assert torch.equal(fused, split)
