@@ -57,3 +57,21 @@ def test_bad_arguments_are_rejected_on_host(lib):
     fake = ctypes.c_void_p(1 << 20)
     assert lib.pfem_build_cells(8, 100, fake, 0, fake, fake, fake, fake, fake, 16, null) == 3
     assert lib.pfem_read_status(null, None, None, null) == 1
+
+
+def test_workspace_sizes_cover_queue_and_records(lib):
+    """Quadratic P2M keeps an SVD-pass queue (8 bytes per node after byte 512) and 136 bytes of
+    node record per node in the workspace; pfem_workspace_size covers both even when the
+    binning scratch is small (few particles on a fine mesh).  The batched workspace covers the
+    records plus an 8-byte node key per node when given the node total, and is the binning
+    scratch alone without it."""
+    n = 1025
+    rec = 4 + 12 + 24 + 24 * 4
+    assert lib.pfem_workspace_size(n, 32, 4096, 4) >= 512 + 8 * n * n + rec * n * n
+    assert lib.pfem_workspace_size(n, 1024, 2048 * 2048, 4) >= 512 + 8 * n * n + rec * n * n
+    nodes = 27_000_000
+    assert lib.pfem_batch_workspace_size(10**6, 250_000, nodes) >= 256 + (rec + 8) * nodes
+    bins_only = lib.pfem_batch_workspace_size(10**6, 250_000, 0)
+    assert bins_only >= 4 * (250_000 + 1) + 8 * 10**6
+    assert bins_only < 256 + (rec + 8) * nodes
+    assert lib.pfem_batch_workspace_size(10**6, 250_000, -1) == 0
