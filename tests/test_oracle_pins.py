@@ -65,15 +65,20 @@ def _incircle_int(a, b, c, d):
             + (cdx * cdx + cdy * cdy) * (adx * bdy - ady * bdx))
 
 
-@pytest.mark.parametrize("jitter", [0.3, 0.0])
+@pytest.mark.parametrize("jitter", [0.3, 0.0, "uniform"])
 def test_delaunay_empty_circles_brute_force(jitter):
     """Every star triangle has an empty circumcircle (App. B, Delaunay definition), checked
     against all particles in exact integer arithmetic; an unjittered lattice (cocircular
-    squares everywhere) only needs 'not strictly inside'."""
+    squares everywhere) only needs 'not strictly inside'.  Also on uniform random particles
+    (no lattice: larger empty circles, star sizes from 3 to 11 here)."""
     M = 20
-    pos = G.jittered_lattice(M, jitter, G.SEED_BASE + 99)
+    if jitter == "uniform":
+        pos = G.uniform01(G.SEED_BASE + 98, 2 * M * M).reshape(M * M, 2)
+    else:
+        pos = G.jittered_lattice(M, jitter, G.SEED_BASE + 99)
     pos = np.round(pos * 4096.0) / 4096.0 % 1.0          # exact small-integer coordinates
     X = np.round(pos * 4096.0).astype(np.int64)
+    assert len({tuple(x) for x in X}) == len(X)           # no duplicates after rounding
     cells = O.build_cells(11, pos)
     N = M * M
     stars = _stars(cells, N)
