@@ -272,7 +272,9 @@ pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bi
  * (pfem_batch_workspace_size with nodes_total, the plan's total nodes): the persistent kernel
  * writes each node's particle set and a second kernel solves its edge systems.  There is no
  * SVD pass here: a node whose moment system the Cholesky solve cannot factor records
- * PFEM_ERR_DEGENERATE. */
+ * PFEM_ERR_DEGENERATE.  nodes_total must be totals[2] of the pfem_batch_plan_init call that
+ * built `plan` (the plan lives on the device and is not read back to check it; 0 always selects
+ * the single fused kernel): the record arrays are laid out for that many nodes. */
 pfem_status pfem_batch_project_p2m(const void *plan, int64_t nodes_total, const void *pos_sorted,
                                    pfem_dtype pos_t,
                                    const uint32_t *q_sorted, const int32_t *cell_start,
