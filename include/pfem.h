@@ -41,6 +41,12 @@
  *    PFEM_F32 or PFEM_BF16 (BF16 is storage only; arithmetic is FP32).  Arithmetic is FP64
  *    when values are PFEM_F64, FP32 otherwise; `solve` selects the precision of the 6x6
  *    moment systems independently.
+ *  - Context: every compute entry point takes a `pfem_ctx *` first.  A context holds the
+ *    options below (caps of the bounded loops, search radii, batch launch shapes) and the text
+ *    of its last host-side error; NULL means the default options, with errors kept per host
+ *    thread.  A context is plain host memory: it allocates nothing on the device, and calls
+ *    with one context from several host threads must not overlap (its error text is shared).
+ *    The paper has no counterpart of contexts or options.
  */
 #ifndef PFEM_H
 #define PFEM_H
@@ -68,12 +74,55 @@ typedef enum { PFEM_SHAPE_LINEAR = 0, PFEM_SHAPE_QUADRATIC = 1 } pfem_shape;
 typedef enum {
     PFEM_SOLVE_F64 = 0,         /* moment assembly and Cholesky in FP64 */
     PFEM_SOLVE_F32 = 1,         /* in FP32 after centring/scaling by the edge length */
-    PFEM_SOLVE_F32_REFINED = 2  /* FP32 Cholesky + one refinement step, FP64 residual */
+    PFEM_SOLVE_F32_REFINED = 2, /* FP32 Cholesky + one refinement step, FP64 residual */
+    PFEM_SOLVE_F32_REFINED_FF = 3 /* FP32 Cholesky + one refinement step, residual in float-float
+                                   (pairs of FP32 numbers, ~48-bit significand): the same
+                                   refinement without FP64 instructions */
 } pfem_solve;
 typedef enum { PFEM_BACKWARD_RECOMPUTE = 0, PFEM_BACKWARD_CHECKPOINT = 1 } pfem_backward_mode;
 
 #define PFEM_KMAX 16        /* max Delaunay neighbours of one particle */
 #define PFEM_KW_MAX 64      /* max weights per node in the explicit-weight form */
+#define PFEM_UMAX 24        /* max distinct particles of one node in the fast pass */
+
+/* Options of a context.  Zero in a field means its default. */
+typedef struct {
+    int32_t walk_max_steps;    /* steps of the visibility walk that locates a mesh node in the
+                                  particles' Delaunay triangulation (default 64); a node that
+                                  needs more records PFEM_ERR_TIMEOUT.  -1: no step allowed */
+    int32_t star_capacity;     /* Delaunay neighbours kept per particle, 3..PFEM_KMAX (default
+                                  PFEM_KMAX); a larger star records PFEM_ERR_CAPACITY */
+    int32_t node_capacity;     /* distinct particles of one node in the fast pass, 3..PFEM_UMAX
+                                  (default PFEM_UMAX); a node with more goes to the fix pass */
+    int32_t search_radius_max; /* widest search, in bins, of the retry and fix passes that take
+                                  the stars and nodes the first search radius could not certify
+                                  (sparse regions, voids); default: a quarter of the torus.  A
+                                  search that exhausts it records PFEM_ERR_CAPACITY */
+    int32_t batch_tile_rows;   /* node rows (4, 8, 16) of a batched P2M work item (default 8) */
+    int32_t batch_p2m_blocks;  /* blocks of the persistent batched P2M (default 8 per SM) */
+    int32_t batch_m2p_blocks;  /* blocks of the batched M2P (default 16 per SM) */
+    int32_t reserved[9];       /* zero */
+} pfem_options;
+
+typedef struct pfem_ctx pfem_ctx;
+
+/* Fill *opt with the defaults (every field explicit). */
+void pfem_options_default(pfem_options *opt);
+
+/* Create a context with the given options (NULL = defaults); *ctx receives it.  Returns
+ * PFEM_ERR_INVALID_ARG for an option out of range (nothing created). */
+pfem_status pfem_create(pfem_ctx **ctx, const pfem_options *opt);
+
+/* Destroy a context (NULL is ignored). */
+void pfem_destroy(pfem_ctx *ctx);
+
+/* The options of a context, defaults filled in (ctx NULL: the defaults). */
+pfem_status pfem_get_options(const pfem_ctx *ctx, pfem_options *opt);
+
+/* Text of the last host-side error of calls made with ctx (ctx NULL: of the calling thread's
+ * calls made without a context), or "" after a call that succeeded.  The pointer stays valid
+ * until the next call with the same context (or on the same thread). */
+const char *pfem_last_error(const pfem_ctx *ctx);
 
 /* Version of this ABI. */
 int pfem_abi_version(void);
@@ -102,6 +151,11 @@ pfem_status pfem_read_status(const void *ws, int32_t *status_host, int64_t *deta
 /* Reset the device status word in `ws` to PFEM_OK (asynchronous). */
 pfem_status pfem_reset_status(void *ws, void *stream);
 
+/* pfem_read_status for a context: the same synchronising read, and a device error is also
+ * described in the context's last-error text. */
+pfem_status pfem_get_device_status(pfem_ctx *ctx, const void *ws, int32_t *status_host,
+                                   int64_t *detail_host, void *stream);
+
 /* a1-a2: canonicalise positions to fixed point and bin the particles with a stable
  * counting sort, slots ordered by (bin, original index).
  *   pos        [N,2] pos_t, original order (device)
@@ -111,7 +165,7 @@ pfem_status pfem_reset_status(void *ws, void *stream);
  *   q_sorted   [N,2] uint32 out: fixed-point coordinates of pos_sorted
  *   ws         workspace of pfem_workspace_size(n, nb, N, C) bytes
  * No paper counterpart: the paper locates particles through CGAL (App. A). */
-pfem_status pfem_build_cells(int32_t nb, int64_t N, const void *pos, pfem_dtype pos_t,
+pfem_status pfem_build_cells(pfem_ctx *ctx, int32_t nb, int64_t N, const void *pos, pfem_dtype pos_t,
                              int32_t *cell_start, int32_t *perm, void *pos_sorted,
                              uint32_t *q_sorted, void *ws, size_t ws_bytes, void *stream);
 
@@ -135,7 +189,7 @@ pfem_status pfem_build_cells_noalloc(int32_t nb, int64_t N, const void *pos, pfe
  * particle, counter-clockwise, in slot indices: nbrs [N, PFEM_KMAX] int32 (unused entries
  * -1), counts [N] int32.  Diagnostic entry point; the projections compute the stars they
  * need on the fly. */
-pfem_status pfem_delaunay_stars(int32_t nb, int64_t N, const uint32_t *q_sorted,
+pfem_status pfem_delaunay_stars(pfem_ctx *ctx, int32_t nb, int64_t N, const uint32_t *q_sorted,
                                 const int32_t *cell_start, int32_t *nbrs, int32_t *counts,
                                 void *ws, size_t ws_bytes, void *stream);
 
@@ -146,7 +200,7 @@ pfem_status pfem_delaunay_stars(int32_t nb, int64_t N, const uint32_t *q_sorted,
  * Used by the checkpointed backward and by pfem_project_p2m with given weights.
  * Quadratic shape functions: the workspace beyond its first 512 bytes holds a queue of the
  * nodes the fast solve cannot take (see pfem_project_p2m). */
-pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+pfem_status pfem_shape_quadratic(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                  pfem_dtype pos_t, const uint32_t *q_sorted,
                                  const int32_t *cell_start, pfem_shape shape, pfem_solve solve,
                                  int32_t K, int32_t *w_idx, void *w, pfem_dtype w_t, void *ws,
@@ -170,7 +224,7 @@ pfem_status pfem_shape_quadratic(int32_t n, int32_t nb, int64_t N, const void *p
  * With FP32 solves and room after the queue for 136 bytes of record per node, the fast pass
  * runs as a geometry kernel and a solve kernel handing over those records; with less, as one
  * fused kernel (same results).  The workspace of pfem_workspace_size() has room for both. */
-pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+pfem_status pfem_project_p2m(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                              pfem_dtype pos_t, const uint32_t *q_sorted,
                              const int32_t *cell_start, const int32_t *perm, int32_t C,
                              const void *vals, pfem_dtype val_t, pfem_shape shape,
@@ -181,7 +235,7 @@ pfem_status pfem_project_p2m(int32_t n, int32_t nb, int64_t N, const void *pos_s
 /* M2P (Sec. 2.2 eq. m2p) with linear FE on the structured mesh, per particle in the order
  * of `pos`:  vals [N, C] val_t out,  mesh_vals [n, n, C] val_t.  C in 1..8.  Needs no
  * workspace and records no device errors. */
-pfem_status pfem_interp_m2p(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
+pfem_status pfem_interp_m2p(pfem_ctx *ctx, int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
                             int32_t C, const void *mesh_vals, void *vals, pfem_dtype val_t,
                             void *stream);
 
@@ -198,7 +252,7 @@ size_t pfem_backward_workspace_size(int32_t n, int64_t N, int32_t K);
  * on the uniform mesh A depends only on the edge direction and is computed once.  Values
  * are read at the unique nodes (I mod (n-1), J mod (n-1)).  FP64 (FP64 positions), FP32 or
  * BF16 storage (FP32 positions).  No workspace, no device errors. */
-pfem_status pfem_interp_m2p_quadratic(int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
+pfem_status pfem_interp_m2p_quadratic(pfem_ctx *ctx, int32_t n, int64_t N, const void *pos, pfem_dtype pos_t,
                                       int32_t C, const void *mesh_vals, void *vals,
                                       pfem_dtype val_t, void *stream);
 
@@ -212,7 +266,7 @@ pfem_status pfem_interp_m2p_quadratic(int32_t n, int64_t N, const void *pos, pfe
  * counting sort (no atomics on values).  Values FP32 (solve F32 or F64) or FP64 (solve F64);
  * ws is a separate workspace of pfem_backward_workspace_size() bytes whose status word records
  * device errors.  A node with more than 32 distinct particles records PFEM_ERR_CAPACITY. */
-pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
+pfem_status pfem_project_backward(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                                   pfem_dtype pos_t, const uint32_t *q_sorted,
                                   const int32_t *cell_start, const int32_t *perm, int32_t C,
                                   const void *vals, pfem_dtype val_t, pfem_shape shape,
@@ -226,7 +280,7 @@ pfem_status pfem_project_backward(int32_t n, int32_t nb, int64_t N, const void *
  *   grad_pos  [N, 2] out (NULL skips): grad_vals . gradient of the linear FE field
  * Deterministic: a per-node gather over the bins' particles (bins must be the
  * pfem_build_cells output for the same positions).  FP32 or FP64 values. */
-pfem_status pfem_interp_m2p_backward(int32_t n, int32_t nb, int64_t N, const void *pos,
+pfem_status pfem_interp_m2p_backward(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos,
                                      pfem_dtype pos_t, const int32_t *cell_start,
                                      const int32_t *perm, int32_t C, const void *mesh_vals,
                                      const void *grad_vals, pfem_dtype val_t, void *grad_mesh,
@@ -252,7 +306,7 @@ size_t pfem_batch_plan_size(int32_t P);
 /* Build the plan (descriptors, search radii, work-item prefix tables) from P host
  * descriptors and copy it to `plan` (device memory of pfem_batch_plan_size(P) bytes); this
  * call synchronises.  totals[0..2] = total particles, total bins, total nodes. */
-pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, void *plan,
+pfem_status pfem_batch_plan_init(pfem_ctx *ctx, int32_t P, const pfem_batch_problem *problems, void *plan,
                                  int64_t *totals);
 
 /* Workspace bytes of pfem_batch_build_cells / pfem_batch_project_p2m for the totals of
@@ -260,31 +314,36 @@ pfem_status pfem_batch_plan_init(int32_t P, const pfem_batch_problem *problems, 
 size_t pfem_batch_workspace_size(int64_t N_total, int64_t bins_total, int64_t nodes_total);
 
 /* Binning of every problem at once (a1-a2 on the concatenated layout). */
-pfem_status pfem_batch_build_cells(const void *plan, int64_t N_total, int64_t bins_total,
+pfem_status pfem_batch_build_cells(pfem_ctx *ctx, const void *plan, int64_t N_total, int64_t bins_total,
                                    const void *pos, pfem_dtype pos_t, int32_t *cell_start,
                                    int32_t *perm, void *pos_sorted, uint32_t *q_sorted, void *ws,
                                    size_t ws_bytes, void *stream);
 
 /* P2M of every problem in one persistent launch: `blocks` blocks of 16 x tile_rows threads
- * (tile_rows 4, 8 or 16) pull (problem, 16 x tile_rows node tile) items from a counter in ws.
- * Values FP32 (FP32 positions) or FP64 (FP64 positions, FP64 solve).  Quadratic shape
- * functions with FP32 solves run as two launches when ws holds the per-node records
- * (pfem_batch_workspace_size with nodes_total, the plan's total nodes): the persistent kernel
- * writes each node's particle set and a second kernel solves its edge systems.  There is no
- * SVD pass here: a node whose moment system the Cholesky solve cannot factor records
- * PFEM_ERR_DEGENERATE.  nodes_total must be totals[2] of the pfem_batch_plan_init call that
- * built `plan` (the plan lives on the device and is not read back to check it; 0 always selects
- * the single fused kernel): the record arrays are laid out for that many nodes. */
-pfem_status pfem_batch_project_p2m(const void *plan, int64_t nodes_total, const void *pos_sorted,
-                                   pfem_dtype pos_t,
+ * (tile_rows 4, 8 or 16; 0 takes the context's batch_tile_rows, blocks 0 its
+ * batch_p2m_blocks) pull (problem, 16 x tile_rows node tile) items from a counter in ws.
+ * Values FP32 (FP32 positions) or FP64 (FP64 positions, FP64 solve).  nodes_total and N_total
+ * must be totals[2] and totals[0] of the pfem_batch_plan_init call that built `plan`; the
+ * workspace (pfem_batch_workspace_size with those totals) holds, after its 256-byte status
+ * block, the fix-pass queue (8 bytes per node), the per-node records and the star table.
+ * Quadratic shape functions then run as for one problem: the star table of every problem, a
+ * persistent kernel that writes each node's record, a kernel that solves the edge systems,
+ * and the fix pass over the queued nodes (FP64, SVD solve, widest search radius).  The
+ * kernels compare the totals with the plan's own before writing anything and record
+ * PFEM_ERR_INVALID_ARG (detail -1) when they differ.  With a smaller workspace (at least 256
+ * bytes plus the queue) every node runs a fused per-node kernel; linear shape functions always
+ * do.  Device errors carry batch-wide node (or particle) indices. */
+pfem_status pfem_batch_project_p2m(pfem_ctx *ctx, const void *plan, int64_t nodes_total,
+                                   int64_t N_total, const void *pos_sorted, pfem_dtype pos_t,
                                    const uint32_t *q_sorted, const int32_t *cell_start,
                                    const int32_t *perm, int32_t C, const void *vals,
                                    pfem_dtype val_t, pfem_shape shape, pfem_solve solve,
                                    void *mesh_vals, int32_t tile_rows, int32_t blocks, void *ws,
                                    size_t ws_bytes, void *stream);
 
-/* M2P of every problem in one launch of `blocks` blocks over 4096-particle chunks. */
-pfem_status pfem_batch_interp_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int32_t C,
+/* M2P of every problem in one launch of `blocks` blocks (0: the context's batch_m2p_blocks)
+ * over 4096-particle chunks. */
+pfem_status pfem_batch_interp_m2p(pfem_ctx *ctx, const void *plan, const void *pos, pfem_dtype pos_t, int32_t C,
                                   const void *mesh_vals, void *vals, pfem_dtype val_t,
                                   int32_t blocks, void *stream);
 

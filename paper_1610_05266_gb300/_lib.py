@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpfem.so")
 
 PFEM_F64, PFEM_F32, PFEM_BF16 = 0, 1, 2
 PFEM_SHAPE_LINEAR, PFEM_SHAPE_QUADRATIC = 0, 1
-PFEM_SOLVE_F64, PFEM_SOLVE_F32, PFEM_SOLVE_F32_REFINED = 0, 1, 2
+PFEM_SOLVE_F64, PFEM_SOLVE_F32, PFEM_SOLVE_F32_REFINED, PFEM_SOLVE_F32_REFINED_FF = 0, 1, 2, 3
 PFEM_BACKWARD_RECOMPUTE, PFEM_BACKWARD_CHECKPOINT = 0, 1
 PFEM_KMAX = 16
 PFEM_KW_MAX = 64
@@ -31,39 +31,54 @@ SIGNATURES = {
     "pfem_abi_version": (ctypes.c_int, []),
     "pfem_launch_count": (ctypes.c_uint64, []),
     "pfem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pfem_options_default": (None, [_p]),
+    "pfem_create": (ctypes.c_int, [ctypes.POINTER(_p), _p]),
+    "pfem_destroy": (None, [_p]),
+    "pfem_get_options": (ctypes.c_int, [_p, _p]),
+    "pfem_last_error": (ctypes.c_char_p, [_p]),
     "pfem_default_bins": (_i32, [_i32, _i64]),
     "pfem_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
     "pfem_read_status": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _p]),
+    "pfem_get_device_status": (ctypes.c_int, [_p, _p, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _p]),
     "pfem_reset_status": (ctypes.c_int, [_p, _p]),
-    "pfem_build_cells": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p, _sz, _p]),
+    "pfem_build_cells": (ctypes.c_int, [_p, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p, _sz, _p]),
     "pfem_build_cells_noalloc": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p]),
-    "pfem_delaunay_stars": (ctypes.c_int, [_i32, _i64, _p, _p, _p, _p, _p, _sz, _p]),
-    "pfem_shape_quadratic": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, ctypes.c_int,
-                                            ctypes.c_int, _i32, _p, _p, ctypes.c_int, _p, _sz, _p]),
-    "pfem_project_p2m": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _i32, _p,
+    "pfem_delaunay_stars": (ctypes.c_int, [_p, _i32, _i64, _p, _p, _p, _p, _p, _sz, _p]),
+    "pfem_shape_quadratic": (ctypes.c_int, [_p, _i32, _i32, _i64, _p, ctypes.c_int, _p, _p,
+                                            ctypes.c_int, ctypes.c_int, _i32, _p, _p, ctypes.c_int,
+                                            _p, _sz, _p]),
+    "pfem_project_p2m": (ctypes.c_int, [_p, _i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _i32, _p,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p, _i32,
                                         ctypes.c_int, _p, _p, _sz, _p]),
-    "pfem_interp_m2p": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int, _p]),
+    "pfem_interp_m2p": (ctypes.c_int, [_p, _i32, _i64, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int, _p]),
     "pfem_backward_workspace_size": (_sz, [_i32, _i64, _i32]),
-    "pfem_interp_m2p_quadratic": (ctypes.c_int, [_i32, _i64, _p, ctypes.c_int, _i32, _p, _p,
+    "pfem_interp_m2p_quadratic": (ctypes.c_int, [_p, _i32, _i64, _p, ctypes.c_int, _i32, _p, _p,
                                                  ctypes.c_int, _p]),
-    "pfem_project_backward": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _i32,
+    "pfem_project_backward": (ctypes.c_int, [_p, _i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _i32,
                                              _p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, _p, _p, _i32, ctypes.c_int, _p, _p, _p,
                                              _p, _sz, _p]),
-    "pfem_interp_m2p_backward": (ctypes.c_int, [_i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _i32,
+    "pfem_interp_m2p_backward": (ctypes.c_int, [_p, _i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _i32,
                                                 _p, _p, ctypes.c_int, _p, _p, _p]),
     "pfem_batch_plan_size": (_sz, [_i32]),
-    "pfem_batch_plan_init": (ctypes.c_int, [_i32, _p, _p, ctypes.POINTER(_i64)]),
+    "pfem_batch_plan_init": (ctypes.c_int, [_p, _i32, _p, _p, ctypes.POINTER(_i64)]),
     "pfem_batch_workspace_size": (_sz, [_i64, _i64, _i64]),
-    "pfem_batch_build_cells": (ctypes.c_int, [_p, _i64, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p,
-                                              _sz, _p]),
-    "pfem_batch_project_p2m": (ctypes.c_int, [_p, _i64, _p, ctypes.c_int, _p, _p, _p, _i32, _p,
-                                              ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _i32,
+    "pfem_batch_build_cells": (ctypes.c_int, [_p, _p, _i64, _i64, _p, ctypes.c_int, _p, _p, _p, _p,
+                                              _p, _sz, _p]),
+    "pfem_batch_project_p2m": (ctypes.c_int, [_p, _p, _i64, _i64, _p, ctypes.c_int, _p, _p, _p, _i32,
+                                              _p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _i32,
                                               _i32, _p, _sz, _p]),
-    "pfem_batch_interp_m2p": (ctypes.c_int, [_p, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int, _i32,
-                                             _p]),
+    "pfem_batch_interp_m2p": (ctypes.c_int, [_p, _p, _p, ctypes.c_int, _i32, _p, _p, ctypes.c_int,
+                                             _i32, _p]),
 }
+
+
+class Options(ctypes.Structure):
+    """pfem_options (include/pfem.h); zero fields take their defaults."""
+    _fields_ = [("walk_max_steps", ctypes.c_int32), ("star_capacity", ctypes.c_int32),
+                ("node_capacity", ctypes.c_int32), ("search_radius_max", ctypes.c_int32),
+                ("batch_tile_rows", ctypes.c_int32), ("batch_p2m_blocks", ctypes.c_int32),
+                ("batch_m2p_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class BatchProblem(ctypes.Structure):
@@ -126,6 +141,14 @@ def stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def check(code: int, what: str):
+def check(code: int, what: str, ctx=None):
+    """Raise PfemError for a non-zero status, with the library's last-error text."""
     if code != 0:
-        raise PfemError(code, what)
+        text = load().pfem_last_error(ctx_ptr(ctx))
+        detail = text.decode() if text else ""
+        raise PfemError(code, f"{what} ({detail})" if detail else what)
+
+
+def ctx_ptr(ctx):
+    """The pfem_ctx* of a Context (or None for the defaults)."""
+    return None if ctx is None else ctx.handle

@@ -13,7 +13,8 @@ import torch
 from . import _lib as L
 from ._lib import (PFEM_BACKWARD_CHECKPOINT, PFEM_BACKWARD_RECOMPUTE, PFEM_F32, PFEM_F64,  # noqa: F401
                    PFEM_KMAX, PFEM_KW_MAX, PFEM_SHAPE_LINEAR, PFEM_SHAPE_QUADRATIC,
-                   PFEM_SOLVE_F32, PFEM_SOLVE_F32_REFINED, PFEM_SOLVE_F64, PfemError, check,
+                   PFEM_SOLVE_F32, PFEM_SOLVE_F32_REFINED, PFEM_SOLVE_F32_REFINED_FF,
+                   PFEM_SOLVE_F64, PfemError, check,
                    dtype_code, ptr, stream_ptr)
 
 
@@ -23,6 +24,40 @@ def pfem_abi_version() -> int:
 
 def pfem_launch_count() -> int:
     return int(L.load().pfem_launch_count())
+
+
+class Context:
+    """A pfem_ctx: options of the bounded searches and loops, and the last host-side error.
+    Keyword arguments are pfem_options fields (walk_max_steps, star_capacity, node_capacity,
+    search_radius_max, batch_tile_rows, batch_p2m_blocks, batch_m2p_blocks); zero or missing
+    fields take their defaults."""
+
+    def __init__(self, **options):
+        lib = L.load()
+        opts = L.Options(**options)
+        h = ctypes.c_void_p()
+        check(lib.pfem_create(ctypes.byref(h), ctypes.byref(opts)), "pfem_create")
+        self.handle = h
+        self._lib = lib
+
+    def options(self) -> dict:
+        o = L.Options()
+        check(self._lib.pfem_get_options(self.handle, ctypes.byref(o)), "pfem_get_options", self)
+        return {name: getattr(o, name) for name, _ in L.Options._fields_ if name != "reserved"}
+
+    def last_error(self) -> str:
+        return pfem_last_error(self)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self._lib.pfem_destroy(h)
+            self.handle = None
+
+
+def pfem_last_error(ctx: Optional[Context] = None) -> str:
+    t = L.load().pfem_last_error(L.ctx_ptr(ctx))
+    return t.decode() if t else ""
 
 
 def pfem_default_bins(n: int, N: int) -> int:
@@ -40,15 +75,28 @@ def pfem_read_status(ws: torch.Tensor, stream=None) -> Tuple[int, int]:
     return code.value, detail.value
 
 
+def pfem_get_device_status(ws: torch.Tensor, stream=None, ctx=None) -> Tuple[int, int]:
+    code, detail = ctypes.c_int32(0), ctypes.c_int64(0)
+    check(L.load().pfem_get_device_status(L.ctx_ptr(ctx), ptr(ws), ctypes.byref(code),
+                                          ctypes.byref(detail), stream_ptr(stream)),
+          "pfem_get_device_status", ctx)
+    return code.value, detail.value
+
+
 def pfem_reset_status(ws: torch.Tensor, stream=None):
     check(L.load().pfem_reset_status(ptr(ws), stream_ptr(stream)), "pfem_reset_status")
 
 
-def pfem_build_cells(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, ws, stream=None):
-    check(L.load().pfem_build_cells(nb, N, ptr(pos), dtype_code(pos.dtype), ptr(cell_start),
-                                    ptr(perm), ptr(pos_sorted), ptr(q_sorted), ptr(ws),
-                                    ws.numel() * ws.element_size(), stream_ptr(stream)),
-          "pfem_build_cells")
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+def pfem_build_cells(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, ws, stream=None,
+                     ctx=None):
+    check(L.load().pfem_build_cells(L.ctx_ptr(ctx), nb, N, ptr(pos), dtype_code(pos.dtype),
+                                    ptr(cell_start), ptr(perm), ptr(pos_sorted), ptr(q_sorted),
+                                    ptr(ws), _nbytes(ws), stream_ptr(stream)),
+          "pfem_build_cells", ctx)
 
 
 def pfem_build_cells_noalloc(nb, N, pos, cell_start, perm, pos_sorted, q_sorted, stream=None):
@@ -58,79 +106,81 @@ def pfem_build_cells_noalloc(nb, N, pos, cell_start, perm, pos_sorted, q_sorted,
                                             stream_ptr(stream)), "pfem_build_cells_noalloc")
 
 
-def pfem_delaunay_stars(nb, N, q_sorted, cell_start, nbrs, counts, ws, stream=None):
-    check(L.load().pfem_delaunay_stars(nb, N, ptr(q_sorted), ptr(cell_start), ptr(nbrs),
-                                       ptr(counts), ptr(ws), ws.numel() * ws.element_size(),
-                                       stream_ptr(stream)), "pfem_delaunay_stars")
+def pfem_delaunay_stars(nb, N, q_sorted, cell_start, nbrs, counts, ws, stream=None, ctx=None):
+    check(L.load().pfem_delaunay_stars(L.ctx_ptr(ctx), nb, N, ptr(q_sorted), ptr(cell_start),
+                                       ptr(nbrs), ptr(counts), ptr(ws), _nbytes(ws),
+                                       stream_ptr(stream)), "pfem_delaunay_stars", ctx)
 
 
 def pfem_shape_quadratic(n, nb, N, pos_sorted, q_sorted, cell_start, shape, solve, K, w_idx, w,
-                         ws, stream=None):
-    check(L.load().pfem_shape_quadratic(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
-                                        ptr(q_sorted), ptr(cell_start), shape, solve, K,
-                                        ptr(w_idx), ptr(w), dtype_code(w.dtype), ptr(ws),
-                                        ws.numel() * ws.element_size(), stream_ptr(stream)),
-          "pfem_shape_quadratic")
+                         ws, stream=None, ctx=None):
+    check(L.load().pfem_shape_quadratic(L.ctx_ptr(ctx), n, nb, N, ptr(pos_sorted),
+                                        dtype_code(pos_sorted.dtype), ptr(q_sorted),
+                                        ptr(cell_start), shape, solve, K, ptr(w_idx), ptr(w),
+                                        dtype_code(w.dtype), ptr(ws), _nbytes(ws),
+                                        stream_ptr(stream)), "pfem_shape_quadratic", ctx)
 
 
 def pfem_project_p2m(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape, solve,
-                     w_idx, w, K, mesh_vals, ws, stream=None):
+                     w_idx, w, K, mesh_vals, ws, stream=None, ctx=None):
     w_t = dtype_code(w.dtype) if w is not None else PFEM_F32
-    check(L.load().pfem_project_p2m(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
-                                    ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
-                                    dtype_code(vals.dtype), shape, solve, ptr(w_idx), ptr(w), K,
-                                    w_t, ptr(mesh_vals), ptr(ws), ws.numel() * ws.element_size(),
-                                    stream_ptr(stream)), "pfem_project_p2m")
+    check(L.load().pfem_project_p2m(L.ctx_ptr(ctx), n, nb, N, ptr(pos_sorted),
+                                    dtype_code(pos_sorted.dtype), ptr(q_sorted), ptr(cell_start),
+                                    ptr(perm), C, ptr(vals), dtype_code(vals.dtype), shape, solve,
+                                    ptr(w_idx), ptr(w), K, w_t, ptr(mesh_vals), ptr(ws),
+                                    _nbytes(ws), stream_ptr(stream)), "pfem_project_p2m", ctx)
 
 
-def pfem_interp_m2p(n, N, pos, C, mesh_vals, vals, stream=None):
-    check(L.load().pfem_interp_m2p(n, N, ptr(pos), dtype_code(pos.dtype), C, ptr(mesh_vals),
-                                   ptr(vals), dtype_code(vals.dtype), stream_ptr(stream)),
-          "pfem_interp_m2p")
+def pfem_interp_m2p(n, N, pos, C, mesh_vals, vals, stream=None, ctx=None):
+    check(L.load().pfem_interp_m2p(L.ctx_ptr(ctx), n, N, ptr(pos), dtype_code(pos.dtype), C,
+                                   ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype),
+                                   stream_ptr(stream)), "pfem_interp_m2p", ctx)
 
 
 def pfem_backward_workspace_size(n: int, N: int, K: int) -> int:
     return int(L.load().pfem_backward_workspace_size(n, N, K))
 
 
-def pfem_interp_m2p_quadratic(n, N, pos, C, mesh_vals, vals, stream=None):
-    check(L.load().pfem_interp_m2p_quadratic(n, N, ptr(pos), dtype_code(pos.dtype), C,
-                                             ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype),
-                                             stream_ptr(stream)), "pfem_interp_m2p_quadratic")
+def pfem_interp_m2p_quadratic(n, N, pos, C, mesh_vals, vals, stream=None, ctx=None):
+    check(L.load().pfem_interp_m2p_quadratic(L.ctx_ptr(ctx), n, N, ptr(pos), dtype_code(pos.dtype),
+                                             C, ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype),
+                                             stream_ptr(stream)), "pfem_interp_m2p_quadratic", ctx)
 
 
 def pfem_project_backward(n, nb, N, pos_sorted, q_sorted, cell_start, perm, C, vals, shape,
                           solve, mode, w_idx, w, K, grad_mesh, grad_vals, grad_pos, ws,
-                          stream=None):
+                          stream=None, ctx=None):
     w_t = dtype_code(w.dtype) if w is not None else PFEM_F32
-    check(L.load().pfem_project_backward(n, nb, N, ptr(pos_sorted), dtype_code(pos_sorted.dtype),
-                                         ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
+    check(L.load().pfem_project_backward(L.ctx_ptr(ctx), n, nb, N, ptr(pos_sorted),
+                                         dtype_code(pos_sorted.dtype), ptr(q_sorted),
+                                         ptr(cell_start), ptr(perm), C, ptr(vals),
                                          dtype_code(vals.dtype), shape, solve, mode, ptr(w_idx),
                                          ptr(w), K, w_t, ptr(grad_mesh), ptr(grad_vals),
-                                         ptr(grad_pos), ptr(ws), ws.numel() * ws.element_size(),
-                                         stream_ptr(stream)), "pfem_project_backward")
+                                         ptr(grad_pos), ptr(ws), _nbytes(ws), stream_ptr(stream)),
+          "pfem_project_backward", ctx)
 
 
 def pfem_interp_m2p_backward(n, nb, N, pos, cell_start, perm, C, mesh_vals, grad_vals, grad_mesh,
-                             grad_pos, stream=None):
-    check(L.load().pfem_interp_m2p_backward(n, nb, N, ptr(pos), dtype_code(pos.dtype),
-                                            ptr(cell_start), ptr(perm), C, ptr(mesh_vals),
-                                            ptr(grad_vals), dtype_code(grad_vals.dtype),
-                                            ptr(grad_mesh), ptr(grad_pos), stream_ptr(stream)),
-          "pfem_interp_m2p_backward")
+                             grad_pos, stream=None, ctx=None):
+    check(L.load().pfem_interp_m2p_backward(L.ctx_ptr(ctx), n, nb, N, ptr(pos),
+                                            dtype_code(pos.dtype), ptr(cell_start), ptr(perm), C,
+                                            ptr(mesh_vals), ptr(grad_vals),
+                                            dtype_code(grad_vals.dtype), ptr(grad_mesh),
+                                            ptr(grad_pos), stream_ptr(stream)),
+          "pfem_interp_m2p_backward", ctx)
 
 
 def pfem_batch_plan_size(P: int) -> int:
     return int(L.load().pfem_batch_plan_size(P))
 
 
-def pfem_batch_plan_init(problems, plan: torch.Tensor):
+def pfem_batch_plan_init(problems, plan: torch.Tensor, ctx=None):
     """problems: list of (n, nb, N).  Returns (N_total, bins_total, nodes_total)."""
     arr = (L.BatchProblem * len(problems))(*[L.BatchProblem(n, nb, N) for n, nb, N in problems])
     tot = (ctypes.c_int64 * 3)()
-    check(L.load().pfem_batch_plan_init(len(problems), ctypes.cast(arr, ctypes.c_void_p), ptr(plan),
-                                        ctypes.cast(tot, ctypes.POINTER(ctypes.c_int64))),
-          "pfem_batch_plan_init")
+    check(L.load().pfem_batch_plan_init(L.ctx_ptr(ctx), len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                        ptr(plan), ctypes.cast(tot, ctypes.POINTER(ctypes.c_int64))),
+          "pfem_batch_plan_init", ctx)
     return int(tot[0]), int(tot[1]), int(tot[2])
 
 
@@ -139,28 +189,28 @@ def pfem_batch_workspace_size(N_total: int, bins_total: int, nodes_total: int = 
 
 
 def pfem_batch_build_cells(plan, N_total, bins_total, pos, cell_start, perm, pos_sorted, q_sorted,
-                           ws, stream=None):
-    check(L.load().pfem_batch_build_cells(ptr(plan), N_total, bins_total, ptr(pos),
+                           ws, stream=None, ctx=None):
+    check(L.load().pfem_batch_build_cells(L.ctx_ptr(ctx), ptr(plan), N_total, bins_total, ptr(pos),
                                           dtype_code(pos.dtype), ptr(cell_start), ptr(perm),
-                                          ptr(pos_sorted), ptr(q_sorted), ptr(ws),
-                                          ws.numel() * ws.element_size(), stream_ptr(stream)),
-          "pfem_batch_build_cells")
+                                          ptr(pos_sorted), ptr(q_sorted), ptr(ws), _nbytes(ws),
+                                          stream_ptr(stream)), "pfem_batch_build_cells", ctx)
 
 
-def pfem_batch_project_p2m(plan, nodes_total, pos_sorted, q_sorted, cell_start, perm, C, vals,
-                           shape, solve, mesh_vals, tile_rows, blocks, ws, stream=None):
-    check(L.load().pfem_batch_project_p2m(ptr(plan), nodes_total, ptr(pos_sorted),
-                                          dtype_code(pos_sorted.dtype),
+def pfem_batch_project_p2m(plan, nodes_total, N_total, pos_sorted, q_sorted, cell_start, perm, C,
+                           vals, shape, solve, mesh_vals, tile_rows, blocks, ws, stream=None,
+                           ctx=None):
+    check(L.load().pfem_batch_project_p2m(L.ctx_ptr(ctx), ptr(plan), nodes_total, N_total,
+                                          ptr(pos_sorted), dtype_code(pos_sorted.dtype),
                                           ptr(q_sorted), ptr(cell_start), ptr(perm), C, ptr(vals),
                                           dtype_code(vals.dtype), shape, solve, ptr(mesh_vals),
-                                          tile_rows, blocks, ptr(ws), ws.numel() * ws.element_size(),
-                                          stream_ptr(stream)), "pfem_batch_project_p2m")
+                                          tile_rows, blocks, ptr(ws), _nbytes(ws),
+                                          stream_ptr(stream)), "pfem_batch_project_p2m", ctx)
 
 
-def pfem_batch_interp_m2p(plan, pos, C, mesh_vals, vals, blocks, stream=None):
-    check(L.load().pfem_batch_interp_m2p(ptr(plan), ptr(pos), dtype_code(pos.dtype), C,
-                                         ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype), blocks,
-                                         stream_ptr(stream)), "pfem_batch_interp_m2p")
+def pfem_batch_interp_m2p(plan, pos, C, mesh_vals, vals, blocks, stream=None, ctx=None):
+    check(L.load().pfem_batch_interp_m2p(L.ctx_ptr(ctx), ptr(plan), ptr(pos), dtype_code(pos.dtype),
+                                         C, ptr(mesh_vals), ptr(vals), dtype_code(vals.dtype),
+                                         blocks, stream_ptr(stream)), "pfem_batch_interp_m2p", ctx)
 
 
 @dataclass
@@ -180,8 +230,10 @@ class Projector:
     """Owns the device buffers for one problem size and runs the round trip through the ABI."""
 
     def __init__(self, n: int, N: int, C: int = 1, nb: Optional[int] = None,
-                 pos_dtype: torch.dtype = torch.float64, device="cuda"):
+                 pos_dtype: torch.dtype = torch.float64, device="cuda",
+                 ctx: Optional[Context] = None):
         self.n, self.N, self.C = n, N, C
+        self.ctx = ctx
         self.nb = nb if nb is not None else pfem_default_bins(n, N)
         self.device = torch.device(device)
         ws_bytes = pfem_workspace_size(n, self.nb, N, C)
@@ -202,7 +254,7 @@ class Projector:
     def build(self, pos: torch.Tensor, stream=None):
         c = self.cells
         pfem_build_cells(self.nb, self.N, pos, c.cell_start, c.perm, c.pos_sorted, c.q_sorted,
-                         c.ws, stream)
+                         c.ws, stream, ctx=self.ctx)
         return c
 
     def p2m(self, vals: torch.Tensor, shape=PFEM_SHAPE_QUADRATIC, solve=None, out=None,
@@ -217,7 +269,7 @@ class Projector:
         K = w_idx.shape[1] if w_idx is not None else 0
         pfem_project_p2m(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
                          None if sorted_vals else c.perm, C, vals, shape, solve, w_idx, w, K, out,
-                         c.ws, stream)
+                         c.ws, stream, ctx=self.ctx)
         return out
 
     def shape_weights(self, shape=PFEM_SHAPE_QUADRATIC, solve=None, K: int = 32,
@@ -230,14 +282,14 @@ class Projector:
         w_idx = torch.empty((nn, K), dtype=torch.int32, device=self.device)
         w = torch.empty((nn, K), dtype=w_dtype, device=self.device)
         pfem_shape_quadratic(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
-                             shape, solve, K, w_idx, w, c.ws, stream)
+                             shape, solve, K, w_idx, w, c.ws, stream, ctx=self.ctx)
         return w_idx, w
 
     def stars(self, stream=None):
         c = self.cells
         nbrs = torch.empty((self.N, PFEM_KMAX), dtype=torch.int32, device=self.device)
         counts = torch.empty(self.N, dtype=torch.int32, device=self.device)
-        pfem_delaunay_stars(self.nb, self.N, c.q_sorted, c.cell_start, nbrs, counts, c.ws, stream)
+        pfem_delaunay_stars(self.nb, self.N, c.q_sorted, c.cell_start, nbrs, counts, c.ws, stream, ctx=self.ctx)
         return nbrs, counts
 
     def m2p(self, pos: torch.Tensor, mesh: torch.Tensor, out=None, shape=PFEM_SHAPE_LINEAR,
@@ -247,9 +299,9 @@ class Projector:
         if out is None:
             out = torch.empty((pos.shape[0], C), dtype=mesh.dtype, device=mesh.device)
         if shape == PFEM_SHAPE_QUADRATIC:
-            pfem_interp_m2p_quadratic(self.n, pos.shape[0], pos, C, mesh, out, stream)
+            pfem_interp_m2p_quadratic(self.n, pos.shape[0], pos, C, mesh, out, stream, ctx=self.ctx)
         else:
-            pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream)
+            pfem_interp_m2p(self.n, pos.shape[0], pos, C, mesh, out, stream, ctx=self.ctx)
         return out
 
     def backward(self, vals: torch.Tensor, grad_mesh: torch.Tensor, shape=PFEM_SHAPE_QUADRATIC,
@@ -273,11 +325,11 @@ class Projector:
         gp = torch.empty((self.N, 2), dtype=vals.dtype, device=self.device) if want_pos else None
         pfem_project_backward(self.n, self.nb, self.N, c.pos_sorted, c.q_sorted, c.cell_start,
                               None if sorted_vals else c.perm, C, vals, shape, solve, mode, w_idx,
-                              w, K, grad_mesh.contiguous(), gv, gp, self._bws, stream)
+                              w, K, grad_mesh.contiguous(), gv, gp, self._bws, stream, ctx=self.ctx)
         return gv, gp
 
     def backward_status(self, stream=None) -> Tuple[int, int]:
-        return pfem_read_status(self._bws, stream)
+        return pfem_get_device_status(self._bws, stream, ctx=self.ctx)
 
     def m2p_backward(self, pos: torch.Tensor, mesh: torch.Tensor, grad_vals: torch.Tensor,
                      want_pos: bool = True, stream=None):
@@ -287,11 +339,11 @@ class Projector:
         gm = torch.empty_like(mesh)
         gp = torch.empty((pos.shape[0], 2), dtype=mesh.dtype, device=self.device) if want_pos else None
         pfem_interp_m2p_backward(self.n, self.nb, pos.shape[0], pos, c.cell_start, c.perm, C,
-                                 mesh.contiguous(), grad_vals.contiguous(), gm, gp, stream)
+                                 mesh.contiguous(), grad_vals.contiguous(), gm, gp, stream, ctx=self.ctx)
         return gm, gp
 
     def status(self, stream=None) -> Tuple[int, int]:
-        return pfem_read_status(self.cells.ws, stream)
+        return pfem_get_device_status(self.cells.ws, stream, ctx=self.ctx)
 
     def reset_status(self, stream=None):
         pfem_reset_status(self.cells.ws, stream)
@@ -310,13 +362,16 @@ class Batch:
     mesh_view(p) of the concatenated mesh output.
     """
 
-    def __init__(self, sizes, C: int, dtype=torch.float32, device="cuda"):
+    def __init__(self, sizes, C: int, dtype=torch.float32, device="cuda",
+                 ctx: Optional[Context] = None):
         self.device = torch.device(device)
+        self.ctx = ctx
         self.C, self.dtype = C, dtype
         self.problems = [(n, pfem_default_bins(n, N), N) for n, N in sizes]
         self.plan = torch.zeros((pfem_batch_plan_size(len(sizes)) + 7) // 8, dtype=torch.float64,
                                 device=self.device)
-        self.N_total, self.bins_total, self.nodes_total = pfem_batch_plan_init(self.problems, self.plan)
+        self.N_total, self.bins_total, self.nodes_total = pfem_batch_plan_init(self.problems, self.plan,
+                                                                               ctx=ctx)
         dev = self.device
         self.cell_start = torch.empty(self.bins_total + 1, dtype=torch.int32, device=dev)
         self.perm = torch.empty(self.N_total, dtype=torch.int32, device=dev)
@@ -331,7 +386,8 @@ class Batch:
             offs.append(offs[-1] + N)
             noffs.append(noffs[-1] + n * n)
         self.offsets, self.node_offsets = offs, noffs
-        self.config = {"tile_rows": 8, "p2m_blocks": 152 * 8, "m2p_blocks": 152 * 16}
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        self.config = {"tile_rows": 8, "p2m_blocks": sms * 8, "m2p_blocks": sms * 16}
         self.graph = None
 
     def mesh_view(self, p: int) -> torch.Tensor:
@@ -340,21 +396,21 @@ class Batch:
 
     def build(self, pos, stream=None):
         pfem_batch_build_cells(self.plan, self.N_total, self.bins_total, pos, self.cell_start,
-                               self.perm, self.pos_sorted, self.q_sorted, self.ws, stream)
+                               self.perm, self.pos_sorted, self.q_sorted, self.ws, stream, ctx=self.ctx)
 
     def p2m(self, vals, shape=PFEM_SHAPE_QUADRATIC, solve=None, tile_rows=None, blocks=None,
             stream=None):
         if solve is None:
             solve = PFEM_SOLVE_F64 if vals.dtype == torch.float64 else PFEM_SOLVE_F32
-        pfem_batch_project_p2m(self.plan, self.nodes_total, self.pos_sorted, self.q_sorted, self.cell_start,
+        pfem_batch_project_p2m(self.plan, self.nodes_total, self.N_total, self.pos_sorted, self.q_sorted, self.cell_start,
                                self.perm, self.C, vals, shape, solve, self.mesh,
                                tile_rows or self.config["tile_rows"],
-                               blocks or self.config["p2m_blocks"], self.ws, stream)
+                               blocks or self.config["p2m_blocks"], self.ws, stream, ctx=self.ctx)
         return self.mesh
 
     def m2p(self, pos, blocks=None, stream=None):
         pfem_batch_interp_m2p(self.plan, pos, self.C, self.mesh, self.back,
-                              blocks or self.config["m2p_blocks"], stream)
+                              blocks or self.config["m2p_blocks"], stream, ctx=self.ctx)
         return self.back
 
     def round_trip(self, pos, vals, shape=PFEM_SHAPE_QUADRATIC, solve=None, stream=None):

@@ -394,7 +394,7 @@ static unsigned grid1(long long work, int threads)
 {
     long long b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152LL * 64) b = 152LL * 64;
+    if (b > num_sms() * 64LL) b = num_sms() * 64LL;
     return (unsigned)b;
 }
 
@@ -416,6 +416,7 @@ BwdLayout bwd_layout(int n, long long N, int Kw)
     L.scan = off;    off = al(off + 4 * scan_scratch_ints(N + 1));
     NodeRecs r;
     L.rec = off;     off = al(off + node_recs_layout(nullptr, (long long)n * n, &r));
+    L.tab = off;     off = al(off + star_tab_bytes(N));
     L.total = off;
     return L;
 }
@@ -461,6 +462,9 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
     b.f.B.nb = g.nb;
     b.f.B.rmax = g.rmax;
     b.f.B.dmax = g.dmax;
+    b.f.B.kcap = g.kcap;
+    b.f.B.walk_cap = g.walk_cap;
+    b.f.ucap = g.ucap;
     b.f.R0 = g.R0;
     b.f.pos = g.pos_sorted;
     b.f.perm = perm;
@@ -481,10 +485,13 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
     // the single fused kernel
     NodeRecs recs;
     node_recs_layout(ws + L.rec, (long long)g.n * g.n, &recs);
+    // the star table's queue counter sits in the status block, after the status word
+    const StarTab tab = star_tab_layout(ws + L.tab, g.N, (int *)(ws + 64));
     const bool split = SHAPE == PFEM_SHAPE_QUADRATIC && sizeof(S) == sizeof(float);
     auto node_pass = [&](bool pos) {
         if (split) {
-            k_p2m_geom<P, V, R><<<grid, 128, 0, s>>>(b.f, recs);
+            launch_star_table(b.f.B, g.R0, g.rmax_far, tab, b.f.status, s);
+            k_p2m_geom<P, V, R><<<grid, 128, 0, s>>>(b.f, tab, recs);
             const unsigned blocks = (unsigned)((recs.nodes + 127) / 128);
             if (pos) k_bwd_solve<P, V, R, S, true><<<blocks, 128, 0, s>>>(b, recs);
             else k_bwd_solve<P, V, R, S, false><<<blocks, 128, 0, s>>>(b, recs);

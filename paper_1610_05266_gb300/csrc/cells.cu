@@ -149,7 +149,7 @@ static unsigned grid_for(long long work, int threads)
 {
     long long b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152LL * 64) b = 152LL * 64;
+    if (b > num_sms() * 64LL) b = num_sms() * 64LL;
     return (unsigned)b;
 }
 

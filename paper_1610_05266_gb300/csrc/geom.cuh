@@ -19,12 +19,19 @@ namespace pfem {
 
 constexpr int KMAX = PFEM_KMAX;
 
+// Internal result of a search that ran out of its region (bins up to rmax) before it could
+// certify its answer: the caller queues the node for a pass with a wider radius.  Not a public
+// status; it becomes PFEM_ERR_CAPACITY where no wider pass follows.
+constexpr int PFEM_FAR = 65;
+
 struct Bins {
     const uint2 *__restrict__ q;      // [N] fixed-point (x, y) in slot order
     const int *__restrict__ start;    // [nb*nb + 1]
     int nb;
     int rmax;                         // largest search radius (bins) tried before giving up
     float dmax;                       // candidate distance cutoff of the first attempt (fixed point)
+    int kcap = KMAX;                  // largest star kept (<= KMAX); larger: PFEM_ERR_CAPACITY
+    int walk_cap = 64;                // visibility-walk steps before PFEM_ERR_TIMEOUT
 };
 
 __device__ __forceinline__ int2 rel(uint2 a, uint2 o)
@@ -259,12 +266,33 @@ __device__ __forceinline__ int fcirc_filter(const FCirc &c, float x, float y)
     return det < -bound ? 1 : (det > bound ? -1 : 0);
 }
 
-template <int KLC = KL>
-static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
-                                             float D, int *nbrs)
+// Candidate list of the list-based star: thread-private arrays, or a thread's column of a
+// shared-memory array (entry k of thread t at k * stride + t).
+template <int KLC> struct LocalList {
+    float2 xy[KLC];
+    int s[KLC];
+    __device__ __forceinline__ float2 at(int k) const { return xy[k]; }
+    __device__ __forceinline__ int slot(int k) const { return s[k]; }
+    __device__ __forceinline__ void put(int k, float2 v, int sl) { xy[k] = v; s[k] = sl; }
+};
+
+struct SmemList {
+    float2 *xy;
+    int *s;
+    int stride;
+    __device__ __forceinline__ float2 at(int k) const { return xy[k * stride]; }
+    __device__ __forceinline__ int slot(int k) const { return s[k * stride]; }
+    __device__ __forceinline__ void put(int k, float2 v, int sl) { xy[k * stride] = v; s[k * stride] = sl; }
+};
+
+// The star of v from the candidates within distance D of it (list capacity KLC), written as
+// out(index, slot) in counter-clockwise order from the nearest neighbour.  Returns the count,
+// -1 when the list overflows or a triangle cannot be certified (the caller tries a wider
+// search), or -PFEM_ERR_*.
+template <int KLC, typename List, typename Out>
+static __device__ __forceinline__ int star_list_into(const Bins &B, int v, uint2 pv,
+                                                     const Region &g, float D, List &L, Out &&out)
 {
-    float2 L[KLC];                  // (x, y) relative to v
-    int Ls[KLC];                    // slots
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
     bool dup = false, over = false;
@@ -278,8 +306,7 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
         const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
         dup |= d2 == 0;
         if (cnt == KLC) { over = true; return; }
-        L[cnt] = make_float2(fx, fy);
-        Ls[cnt] = s;
+        L.put(cnt, make_float2(fx, fy), s);
         if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; }
         ++cnt;
     });
@@ -288,16 +315,16 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
     const float clx = g.cl_lo_x, chx = g.cl_hi_x, cly = g.cl_lo_y, chy = g.cl_hi_y;
     int cur = u0, n = 0;
     for (;;) {
-        if (n == KMAX) return -PFEM_ERR_CAPACITY;
-        const float2 W = L[cur];
-        const int wslot = Ls[cur];
-        nbrs[n++] = wslot;
+        if (n == B.kcap) return -PFEM_ERR_CAPACITY;
+        const float2 W = L.at(cur);
+        const int wslot = L.slot(cur);
+        out(n++, wslot);
         const float wx = W.x, wy = W.y, lw = fmaf(wx, wx, wy * wy);
         int best = -1;
         FCirc cb;
         cb.K = cb.P = cb.Q = cb.Ka = cb.Pa = cb.Qa = 0.f;
         for (int k = 0; k < cnt; ++k) {
-            const float2 c2 = L[k];
+            const float2 c2 = L.at(k);
             const float4 c = make_float4(c2.x, c2.y, fmaf(c2.x, c2.x, c2.y * c2.y), 0.f);
             // orientation of (v, w, c): FP32 filter
             const float o1 = wx * c.y, o2 = wy * c.x;
@@ -306,7 +333,7 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
             bool left = o > ob;
             if (fabsf(o) <= ob && k != cur) {            // rare: decide exactly
                 const int2 dw = rel(__ldg(B.q + wslot), pv);
-                const int2 dc = rel(__ldg(B.q + Ls[k]), pv);
+                const int2 dc = rel(__ldg(B.q + L.slot(k)), pv);
                 left = cross(dw, dc) > 0;
             }
             if (!left) continue;
@@ -317,8 +344,8 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
                 const float bnd = 1.9073486328125e-06f * mag;
                 int t = det < -bnd ? 1 : (det > bnd ? -1 : 0);
                 if (t == 0) {                              // rare: decide exactly
-                    const uint2 qw = __ldg(B.q + wslot), qb = __ldg(B.q + Ls[best]),
-                                qc = __ldg(B.q + Ls[k]);
+                    const uint2 qw = __ldg(B.q + wslot), qb = __ldg(B.q + L.slot(best)),
+                                qc = __ldg(B.q + L.slot(k));
                     t = incircle_exact(rel(qw, pv), rel(qb, pv), rel(qc, pv), pv, qw, qb, qc);
                 }
                 if (t < 0) continue;
@@ -349,6 +376,21 @@ static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, 
     return n >= 3 ? n : -1;
 }
 
+template <int KLC = KL>
+static __device__ __forceinline__ int star_list(const Bins &B, int v, uint2 pv, const Region &g,
+                                             float D, int *nbrs)
+{
+    LocalList<KLC> L;
+    return star_list_into<KLC>(B, v, pv, g, D, L, [&](int k, int s) { nbrs[k] = s; });
+}
+
+// Next search radius: one bin at a time near the first radius, then by a quarter (a large void
+// needs few attempts; any radius that certifies a result gives the same, unique result).
+__device__ __forceinline__ int next_radius(int R, int R0)
+{
+    return R < R0 + 3 ? R + 1 : R + max(1, R >> 2);
+}
+
 // Star of v by gift-wrapping over every particle of growing regions (no distance cutoff): the
 // path of a star the list attempt could not certify.
 static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, int R0, int *nbrs)
@@ -365,7 +407,7 @@ static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, i
             if (c != -1) return c;
         }
     }
-    for (int attempt = 1, R = R0; R <= B.rmax; ++attempt, R += attempt > 1 ? 1 : 0) {
+    for (int R = R0; R <= B.rmax; R = next_radius(R, R0)) {
         const float dmax = 0.f;
         const Region g = make_region(B, pv, R);
         int u0 = -1;
@@ -386,7 +428,7 @@ static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, i
         int cur = u0, cnt = 0;
         bool ok = true;
         for (;;) {
-            if (cnt == KMAX) return -PFEM_ERR_CAPACITY;
+            if (cnt == B.kcap) return -PFEM_ERR_CAPACITY;
             nbrs[cnt++] = cur;
             const int a = apex_search(B, pv, __ldg(B.q + cur), g, dmax);
             if (a < 0) { ok = false; break; }
@@ -395,7 +437,7 @@ static __device__ __noinline__ int star_region(const Bins &B, int v, uint2 pv, i
         }
         if (ok && cnt >= 3) return cnt;
     }
-    return -PFEM_ERR_CAPACITY;
+    return -PFEM_FAR;
 }
 
 // Counter-clockwise Delaunay star of slot v into nbrs[0..count), starting at v's nearest
@@ -416,21 +458,18 @@ __device__ __forceinline__ int apex_of(const Bins &B, int u, int w, int R0)
     const uint2 pu = __ldg(B.q + u), pw = __ldg(B.q + w);
     const int a0 = apex_search(B, pu, pw, make_region(B, pu, R0), B.dmax);
     if (a0 >= 0) return a0;
-    for (int R = R0; R <= B.rmax; ++R) {
+    for (int R = R0; R <= B.rmax; R = next_radius(R, R0)) {
         const int a = apex_search(B, pu, pw, make_region(B, pu, R));
         if (a >= 0) return a;
     }
     return -1;
 }
 
-// Locate fixed-point point p in the Delaunay triangulation: tri = counter-clockwise triangle
-// containing p (boundary included).  On success also returns the star of tri[0] in star0
-// (count n0) when tri[0] is the particle nearest to p, else n0 = 0.  Returns 0 or -PFEM_ERR_*.
-static __device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tri[3], int *star0, int &n0)
+// The particle nearest to fixed-point point p (lowest slot among equals), certified by the
+// searched region's clearance; -PFEM_FAR when no region up to rmax certifies it.
+__device__ __forceinline__ int nearest_particle(const Bins &B, uint2 p, int R0)
 {
-    n0 = 0;
-    int v0 = -1;
-    for (int R = R0; R <= B.rmax && v0 < 0; ++R) {
+    for (int R = R0; R <= B.rmax; R = next_radius(R, R0)) {
         const Region g = make_region(B, p, R);
         long long d2b = 0x7fffffffffffffffLL;
         int best = -1;
@@ -443,40 +482,47 @@ static __device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tr
             }
         });
         const float clm = fminf(fminf(g.cl_lo_x, g.cl_hi_x), fminf(g.cl_lo_y, g.cl_hi_y));
-        if (best >= 0 && (float)d2b * 1.0001f < clm * clm) v0 = best;
+        if (best >= 0 && (float)d2b * 1.0001f < clm * clm) return best;
     }
-    if (v0 < 0) return -PFEM_ERR_CAPACITY;
-    const int cnt = star_of(B, v0, R0, star0);
-    if (cnt < 0) return cnt;
+    return -PFEM_FAR;
+}
+
+// The triangle containing p, given the particle v0 nearest to p and its counter-clockwise star
+// s0 (cnt entries, any indexable type): the sector of v0's fan that holds p, else a visibility
+// walk from that sector's outer edge, stepping through apex(u, w) = the apex of the triangle to
+// the left of the directed edge u -> w.  tri = counter-clockwise triangle, with tri[0] = v0 when
+// p lies in v0's fan.  Returns 0 or -PFEM_ERR_* / -PFEM_FAR.
+template <typename SA, typename Apex>
+__device__ __forceinline__ int fan_walk(const Bins &B, uint2 p, int v0, const SA &s0, int cnt,
+                                        Apex &&apex, int tri[3])
+{
     const uint2 q0 = __ldg(B.q + v0);
     const int2 dp = rel(p, q0);
     if (dp.x == 0 && dp.y == 0) {
-        tri[0] = v0; tri[1] = star0[0]; tri[2] = star0[1];
-        n0 = cnt;
+        tri[0] = v0; tri[1] = s0[0]; tri[2] = s0[1];
         return 0;
     }
     // sector of the fan around v0 that holds p: [st[j], st[j+1]) counter-clockwise
     int j = -1;
-    int2 da = rel(__ldg(B.q + star0[cnt - 1]), q0);
+    int2 da = rel(__ldg(B.q + s0[cnt - 1]), q0);
     for (int k = 0; k < cnt; ++k) {
-        const int2 dn = rel(__ldg(B.q + star0[k]), q0);
+        const int2 dn = rel(__ldg(B.q + s0[k]), q0);
         if (cross(da, dp) >= 0 && cross(dn, dp) < 0) { j = (k + cnt - 1) % cnt; break; }
         da = dn;
     }
     if (j < 0) return -PFEM_ERR_DEGENERATE;
-    int e0 = star0[j], e1 = star0[(j + 1) % cnt];
+    int e0 = s0[j], e1 = s0[(j + 1) % cnt];
     {
         const int2 a = rel(__ldg(B.q + e0), p), b = rel(__ldg(B.q + e1), p);
         if (cross(a, b) >= 0) {                       // orient(e0, e1, p) >= 0
             tri[0] = v0; tri[1] = e0; tri[2] = e1;
-            n0 = cnt;
             return 0;
         }
     }
     // visibility walk: p is strictly right of e0 -> e1; step into the triangle beyond.
-    for (int step = 0; step < 64; ++step) {
-        const int x = apex_of(B, e1, e0, R0);
-        if (x < 0) return -PFEM_ERR_CAPACITY;
+    for (int step = 0; step < B.walk_cap; ++step) {
+        const int x = apex(e1, e0);
+        if (x < 0) return x == -1 ? -PFEM_FAR : x;
         const int2 a = rel(__ldg(B.q + e0), p), b = rel(__ldg(B.q + e1), p),
                    c = rel(__ldg(B.q + x), p);
         if (cross(a, c) < 0) { e1 = x; continue; }   // p strictly right of e0 -> x
@@ -485,6 +531,23 @@ static __device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tr
         return 0;
     }
     return -PFEM_ERR_TIMEOUT;
+}
+
+// Locate fixed-point point p in the Delaunay triangulation: tri = counter-clockwise triangle
+// containing p (boundary included).  On success also returns the star of tri[0] in star0
+// (count n0) when tri[0] is the particle nearest to p, else n0 = 0.  Returns 0 or -PFEM_ERR_*
+// (-PFEM_FAR: a search region reached rmax).
+static __device__ __noinline__ int locate(const Bins &B, uint2 p, int R0, int tri[3], int *star0, int &n0)
+{
+    n0 = 0;
+    const int v0 = nearest_particle(B, p, R0);
+    if (v0 < 0) return v0;
+    const int cnt = star_of(B, v0, R0, star0);
+    if (cnt < 0) return cnt;
+    const int st = fan_walk(B, p, v0, star0, cnt, [&](int u, int w) { return apex_of(B, u, w, R0); },
+                            tri);
+    if (st == 0 && tri[0] == v0) n0 = cnt;
+    return st;
 }
 
 }  // namespace pfem

@@ -13,6 +13,9 @@ namespace pfem {
 // Launch counter behind pfem_launch_count(); every kernel launch site calls count_launch().
 void count_launch(unsigned k = 1);
 
+// Multiprocessors of the current device (queried once per device), for grid sizes.
+int num_sms();
+
 // Byte offsets of the workspace regions (the status word always sits at offset 0).
 struct WsLayout {
     size_t status, count, key, rank, scan, bwd, total;
@@ -33,9 +36,9 @@ cudaError_t launch_batch_build_cells(const void *plan, long long Ntot, long long
 cudaError_t launch_batch_p2m(const void *plan, const void *pos_sorted, const uint32_t *q_sorted,
                              const int *cell_start, const int *perm, int C, const void *vals,
                              pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *mesh,
-                             int shape_idx, int blocks, long long nodes_total, void *ws,
-                             size_t ws_bytes, cudaStream_t s);
-size_t batch_p2m_ws_bytes(long long nodes_total);
+                             int shape_idx, int blocks, long long nodes_total, long long N_total,
+                             void *ws, size_t ws_bytes, cudaStream_t s);
+size_t batch_p2m_ws_bytes(long long nodes_total, long long N_total);
 cudaError_t launch_batch_m2p(const void *plan, const void *pos, pfem_dtype pos_t, int C,
                              const void *mesh, void *vals, pfem_dtype val_t, int blocks,
                              cudaStream_t s);
@@ -55,14 +58,27 @@ struct GeoArgs {
     const int *cell_start;
     int R0, rmax;
     float dmax;
-    bool tiled;                 // fused P2M may use the tiled kernel
+    int rmax_far;               // search radius (bins) of the retry and fix passes
+    int kcap;                   // star capacity (<= PFEM_KMAX)
+    int walk_cap;               // visibility-walk steps
+    int ucap;                   // distinct particles of one node in the fast pass (<= PFEM_UMAX)
 };
+
+struct StarTab;
+struct Bins;
+// Star table (startab.cuh): bytes for N particles, its layout from `base` (qcount: the queue
+// counter), and the launches that fill it.
+size_t star_tab_bytes(long long N);
+StarTab star_tab_layout(char *base, long long N, int *qcount);
+cudaError_t launch_star_table(const Bins &B, int R0, int rmax_far, const StarTab &t,
+                              DevStatus *st, cudaStream_t s);
 
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
                        pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,
                        DevStatus *st, size_t ws_bytes, cudaStream_t s);
-// Workspace bytes quadratic P2M uses for n*n nodes (queue + node records of the two-kernel path).
-size_t p2m_ws_bytes(long long nodes);
+// Workspace bytes P2M uses for n*n nodes and N particles (fix-pass queue, node records, star
+// table).
+size_t p2m_ws_bytes(long long nodes, long long N);
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
                          void *w, pfem_dtype w_t, DevStatus *st, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_dtype val_t,
@@ -76,7 +92,7 @@ cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, in
 
 struct BwdLayout {
     int K;   // entries per node written by the recompute kernel
-    size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, rec, total;   // rec: node records
+    size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, rec, tab, total;   // rec: node records, tab: star table
 };
 BwdLayout bwd_layout(int n, long long N, int K);
 

@@ -66,7 +66,7 @@ static cudaError_t m2p_t(int n, long long N, const void *pos, int C, const void 
                          cudaStream_t s)
 {
     long long blocks = (N + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks > num_sms() * 16LL) blocks = num_sms() * 16LL;
     if (blocks < 1) blocks = 1;
     const bool aligned = ((reinterpret_cast<uintptr_t>(mesh) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0;
     if (C == 4 && aligned)
@@ -195,7 +195,7 @@ static cudaError_t m2p_bwd_t(int n, int nb, long long N, const void *pos, const 
     count_launch();
     if (gp && N > 0) {
         long long blocks = (N + 255) / 256;
-        if (blocks > 152LL * 16) blocks = 152LL * 16;
+        if (blocks > num_sms() * 16LL) blocks = num_sms() * 16LL;
         k_m2p_bwd_pos<P, V, R><<<(unsigned)blocks, 256, 0, s>>>(n, N, (const P *)pos, C,
                                                                (const V *)mesh, (const V *)gv,
                                                                (V *)gp);
@@ -409,7 +409,7 @@ cudaError_t launch_m2p_quadratic(int n, long long N, const void *pos, pfem_dtype
     if (N == 0) return cudaSuccess;
     const MQTable &T = mq_table();
     long long blocks = (N + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks > num_sms() * 16LL) blocks = num_sms() * 16LL;
     const bool aligned = ((reinterpret_cast<uintptr_t>(mesh) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0;
     if (val_t == PFEM_F64 && pos_t == PFEM_F64)
         k_m2p_q<double, double, double, 0><<<(unsigned)blocks, 256, 0, s>>>(n, N, (const double *)pos, C, (const double *)mesh, (double *)vals, T);

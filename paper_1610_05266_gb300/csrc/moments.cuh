@@ -86,6 +86,61 @@ template <typename S> struct Moment {
     }
 };
 
+// ----------------------------------------------------------------- float-float arithmetic
+// An unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits), built from the
+// error-free transformations of Dekker (1971) and Knuth (TAOCP vol. 2, 4.2.2): the FP32 sum and
+// product of two floats are exact once their rounding error is carried along.  Used for the
+// residual of the refined FP32 solve, which must be formed in about twice the working
+// precision; on sm_103a FP32 instructions issue at 64 times the rate of FP64 ones.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ FF ff_two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ FF ff_norm(float h, float l)
+{
+    const float s = h + l;
+    return {s, l - (s - h)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const FF s = ff_two_sum(a.h, b.h);
+    return ff_norm(s.h, s.l + (a.l + b.l));
+}
+
+// (a.h + a.l) * b for a float b
+__device__ __forceinline__ FF ff_mul(FF a, float b)
+{
+    const FF p = ff_two_prod(a.h, b);
+    return ff_norm(p.h, fmaf(a.l, b, p.l));
+}
+
+// (a.h + a.l) * (b.h + b.l)
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const FF p = ff_two_prod(a.h, b.h);
+    return ff_norm(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+
+// Refinement of the FP32 moment solve: 0 = none, 1 = residual in FP64, 2 = residual in
+// float-float.
+enum { REFINE_NONE = 0, REFINE_F64 = 1, REFINE_FF = 2 };
+
 template <typename S> struct SolveTol;
 template <> struct SolveTol<double> { static constexpr double v = 1e-13; };
 template <> struct SolveTol<float> { static constexpr float v = 1e-6f; };

@@ -4,7 +4,7 @@
 #include <climits>
 
 #include "internal.h"
-#include "p2m_tiled.cuh"
+#include "p2m.cuh"
 
 namespace pfem {
 
@@ -29,6 +29,8 @@ static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
     a.B.nb = g.nb;
     a.B.rmax = g.rmax;
     a.B.dmax = g.dmax;
+    a.B.kcap = g.kcap;
+    a.B.walk_cap = g.walk_cap;
     a.R0 = g.R0;
     a.pos = g.pos_sorted;
     a.perm = nullptr;
@@ -39,37 +41,15 @@ static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
     a.w = nullptr;
     a.K = 0;
     a.status = st;
+    a.ucap = g.ucap;
     return a;
 }
 
 static dim3 node_grid(int n) { return dim3((n + 15) / 16, (n + 7) / 8); }
 
-// Nodes per tile side for the tiled kernel (0: use the per-thread kernel): the staged window
-// (tile bins + halo) must fit the shared-memory capacity and stay within half the torus.
-int tile_side(int n, int nb, long long N)
+template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
+static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s)
 {
-    const double bins_per_cell = (double)nb / (double)(n - 1);
-    const double ppb = (double)N / ((double)nb * nb);
-    for (int T = 16; T >= 4; T >>= 1) {
-        const int w = (int)ceil((T - 1) * bins_per_cell) + 2 + 2 * THB;
-        if (w * w <= TMAXB && 2 * w <= nb && w * w * ppb * 1.1 <= TMAXP) return T;
-    }
-    return 0;
-}
-
-template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
-static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s, int T)
-{
-    if (!W && T > 0) {
-        auto k = k_p2m_tiled<P, V, R, S, REF, SHAPE>;
-        const int bytes = (int)sizeof(TileSmem);
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        const int tx = (a.n + T - 1) / T;
-        k<<<tx * tx, TT, bytes, s>>>(a, T, tx);
-        count_launch();
-        return cudaGetLastError();
-    }
     k_p2m<P, V, R, S, REF, SHAPE, W><<<node_grid(a.n), 128, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
@@ -77,37 +57,46 @@ static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s, int T)
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Workspace layout of quadratic P2M after the 256-byte status block: the queue counter at 256,
-// the queue from 512 (8 bytes per node), then the node records of the two-kernel path.
+// Workspace layout of P2M after the 256-byte status block: the fix-pass queue counter at byte
+// 256 and the star-table queue counter at byte 260, the fix-pass queue from byte 512 (8 bytes
+// per node), then the node records and the star table of the table path.
 static size_t recs_offset(long long nodes) { return al256(512 + 8 * (size_t)nodes); }
 
-size_t p2m_ws_bytes(long long nodes)
+size_t p2m_ws_bytes(long long nodes, long long N)
 {
     NodeRecs r;
-    return recs_offset(nodes) + node_recs_layout(nullptr, nodes, &r);
+    const size_t recs = al256(node_recs_layout(nullptr, nodes, &r));
+    return recs_offset(nodes) + recs + star_tab_bytes(N);
 }
 
-static bool set_recs(NodeRecs &r, void *ws, size_t ws_bytes, long long nodes)
+// Records and star table in ws, when it has room for them.
+static bool set_table(NodeRecs &r, StarTab &t, void *ws, size_t ws_bytes, long long nodes,
+                      long long N)
 {
-    if (ws_bytes < p2m_ws_bytes(nodes)) return false;
-    node_recs_layout((char *)ws + recs_offset(nodes), nodes, &r);
+    if (ws_bytes < p2m_ws_bytes(nodes, N)) return false;
+    char *base = (char *)ws + recs_offset(nodes);
+    const size_t recs = al256(node_recs_layout(base, nodes, &r));
+    t = star_tab_layout(base + recs, N, (int *)((char *)ws + 260));
     return true;
 }
 
-// Fused P2M: the fast pass over all nodes (one kernel, or with node records and FP32 solves
-// the geometry and solve kernels), then (quadratic shape functions, with a queue) the FP64 SVD pass over the
-// nodes it queued.
-template <typename P, typename V, typename R, typename S, bool REF, int SHAPE, bool W>
-static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0, const NodeRecs *rec = nullptr)
+// P2M: the fast pass over all nodes, then the fix pass over the nodes it queued.  With quadratic
+// shape functions, the apply form and room for the table, the fast pass is the star table, the
+// geometry kernel (node records) and the solve kernel; otherwise one kernel that searches the
+// stars per node.
+template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
+static cudaError_t go(const P2MArgs &a, int R0, int rmax_far, cudaStream_t s,
+                      const NodeRecs *rec = nullptr, const StarTab *tab = nullptr)
 {
-    const bool queue = SHAPE == PFEM_SHAPE_QUADRATIC && a.defer_cap > 0;
-    if (queue) {
-        cudaError_t e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
+    cudaError_t e;
+    if (a.defer_cap > 0) {
+        e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e;
-    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && T == 0 && rec && sizeof(S) == sizeof(float)) {
-        k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *rec);
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab) {
+        e = launch_star_table(a.B, R0, rmax_far, *tab, a.status, s);
+        if (e != cudaSuccess) return e;
+        k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *tab, *rec);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -115,12 +104,27 @@ static cudaError_t go(const P2MArgs &a, cudaStream_t s, int T = 0, const NodeRec
         count_launch();
         e = cudaGetLastError();
     } else {
-        e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s, T);
+        e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s);
     }
-    if (e != cudaSuccess || !queue) return e;
-    k_p2m_fix<P, V, R, W><<<152, 128, 0, s>>>(a);
+    if (e != cudaSuccess || a.defer_cap <= 0) return e;
+    P2MArgs f = a;
+    f.B.rmax = rmax_far > a.B.rmax ? rmax_far : a.B.rmax;
+    k_p2m_fix<P, V, R, SHAPE, W><<<num_sms(), 128, 0, s>>>(f);
     count_launch();
     return cudaGetLastError();
+}
+
+// Compute type S and refinement of each solve for FP32 arithmetic.
+template <typename P, typename V, int SHAPE, bool W>
+static cudaError_t go_solve(pfem_solve solve, const P2MArgs &a, int R0, int rmax_far,
+                            cudaStream_t s, const NodeRecs *r, const StarTab *t)
+{
+    switch (solve) {
+    case PFEM_SOLVE_F64: return go<P, V, float, double, REFINE_NONE, SHAPE, W>(a, R0, rmax_far, s, r, t);
+    case PFEM_SOLVE_F32: return go<P, V, float, float, REFINE_NONE, SHAPE, W>(a, R0, rmax_far, s, r, t);
+    case PFEM_SOLVE_F32_REFINED: return go<P, V, float, float, REFINE_F64, SHAPE, W>(a, R0, rmax_far, s, r, t);
+    default: return go<P, V, float, float, REFINE_FF, SHAPE, W>(a, R0, rmax_far, s, r, t);
+    }
 }
 
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
@@ -134,23 +138,22 @@ cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *val
     a.C = C;
     a.out = out;
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
-    const int T = g.tiled ? tile_side(g.n, g.nb, g.N) : 0;
     NodeRecs recs;
-    const NodeRecs *r = set_recs(recs, st, ws_bytes, (long long)g.n * g.n) ? &recs : nullptr;
+    StarTab tab;
+    const bool table = set_table(recs, tab, st, ws_bytes, (long long)g.n * g.n, g.N);
+    const NodeRecs *r = table ? &recs : nullptr;
+    const StarTab *t = table ? &tab : nullptr;
+    const int R0 = g.R0, rf = g.rmax_far;
     if (val_t == PFEM_F64) {   // positions FP64, arithmetic FP64
-        if (!q) return go<double, double, double, double, false, 0, false>(a, s, T);
-        return go<double, double, double, double, false, 1, false>(a, s, T, r);
+        if (!q) return go<double, double, double, double, REFINE_NONE, 0, false>(a, R0, rf, s);
+        return go<double, double, double, double, REFINE_NONE, 1, false>(a, R0, rf, s, r, t);
     }
     if (val_t == PFEM_F32) {   // positions FP32, arithmetic FP32
-        if (!q) return go<float, float, float, float, false, 0, false>(a, s, T);
-        if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, false>(a, s, T, r);
-        if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, false>(a, s, T, r);
-        return go<float, float, float, float, true, 1, false>(a, s, T, r);
+        if (!q) return go<float, float, float, float, REFINE_NONE, 0, false>(a, R0, rf, s);
+        return go_solve<float, float, 1, false>(solve, a, R0, rf, s, r, t);
     }
-    if (!q) return go<float, __nv_bfloat16, float, float, false, 0, false>(a, s, T);
-    if (solve == PFEM_SOLVE_F64) return go<float, __nv_bfloat16, float, double, false, 1, false>(a, s, T, r);
-    if (solve == PFEM_SOLVE_F32) return go<float, __nv_bfloat16, float, float, false, 1, false>(a, s, T, r);
-    return go<float, __nv_bfloat16, float, float, true, 1, false>(a, s, T, r);
+    if (!q) return go<float, __nv_bfloat16, float, float, REFINE_NONE, 0, false>(a, R0, rf, s);
+    return go_solve<float, __nv_bfloat16, 1, false>(solve, a, R0, rf, s, r, t);
 }
 
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
@@ -162,14 +165,13 @@ cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, i
     a.w_idx = w_idx;
     a.w = w;
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
+    const int R0 = g.R0, rf = g.rmax_far;
     if (w_t == PFEM_F64) {
-        if (!q) return go<double, double, double, double, false, 0, true>(a, s);
-        return go<double, double, double, double, false, 1, true>(a, s);
+        if (!q) return go<double, double, double, double, REFINE_NONE, 0, true>(a, R0, rf, s);
+        return go<double, double, double, double, REFINE_NONE, 1, true>(a, R0, rf, s);
     }
-    if (!q) return go<float, float, float, float, false, 0, true>(a, s);
-    if (solve == PFEM_SOLVE_F64) return go<float, float, float, double, false, 1, true>(a, s);
-    if (solve == PFEM_SOLVE_F32) return go<float, float, float, float, false, 1, true>(a, s);
-    return go<float, float, float, float, true, 1, true>(a, s);
+    if (!q) return go<float, float, float, float, REFINE_NONE, 0, true>(a, R0, rf, s);
+    return go_solve<float, float, 1, true>(solve, a, R0, rf, s, nullptr, nullptr);
 }
 
 // alpha_i = sum_k w[i,k] alpha[w_idx[i,k]] (explicit-weight P2M)
@@ -203,7 +205,7 @@ cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_d
 {
     const long long nodes = (long long)n * n;
     long long blocks = (nodes + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks > num_sms() * 16LL) blocks = num_sms() * 16LL;
     if (val_t == PFEM_F64 && w_t == PFEM_F64)
         k_apply<double, double><<<(unsigned)blocks, 256, 0, s>>>(
             nodes, K, w_idx, (const double *)w, perm, C, (const double *)vals, (double *)out);
@@ -238,7 +240,7 @@ cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st
 {
     P2MArgs a = make_args(g, st);
     long long blocks = (g.N + 127) / 128;
-    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    if (blocks > num_sms() * 32LL) blocks = num_sms() * 32LL;
     if (blocks < 1) blocks = 1;
     k_stars<<<(unsigned)blocks, 128, 0, s>>>(a.B, g.R0, g.N, nbrs, counts, st);
     count_launch();

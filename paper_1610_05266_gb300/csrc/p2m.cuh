@@ -11,6 +11,7 @@
 
 #include "geom.cuh"
 #include "moments.cuh"
+#include "startab.cuh"
 
 namespace pfem {
 
@@ -32,6 +33,10 @@ struct P2MArgs {
     int *defer_count = nullptr;
     long long *defer_list = nullptr;
     int defer_cap = 0;
+    // Index of this problem's first node in a batch (0 for one problem): queue entries and
+    // error details are node indices of the whole batch.
+    long long noff = 0;
+    int ucap = PFEM_UMAX;       // distinct particles of one node in the fast pass
 };
 
 // node_quadratic's code for "queue this node for the FP64 SVD pass" (not a public status), and
@@ -39,12 +44,14 @@ struct P2MArgs {
 constexpr int PFEM_DEFER = 64;
 constexpr int PFEM_DEFERRED = 1;
 
-// A node whose moment system the fast solve could not factor is queued for the FP64 SVD pass
-// (returns PFEM_DEFERRED), or, with no room in the queue, becomes an error code.
+// A node whose moment system the fast solve could not factor, or whose search ran out of its
+// region (-PFEM_FAR), is queued for the fix pass (FP64, SVD solve, widest search radius) and
+// returns PFEM_DEFERRED; with no queue (the fix pass itself, or a workspace without room) it
+// becomes PFEM_ERR_DEGENERATE or PFEM_ERR_CAPACITY.
 __device__ __forceinline__ int defer_or_error(const P2MArgs &a, int st, long long node)
 {
-    if (st != -PFEM_DEFER) return st;
-    if (a.defer_cap <= 0) return -PFEM_ERR_DEGENERATE;
+    if (st != -PFEM_DEFER && st != -PFEM_FAR) return st;
+    if (a.defer_cap <= 0) return st == -PFEM_FAR ? -PFEM_ERR_CAPACITY : -PFEM_ERR_DEGENERATE;
     const int i = atomicAdd(a.defer_count, 1);
     if (i >= a.defer_cap) return -PFEM_ERR_CAPACITY;
     a.defer_list[i] = node;
@@ -211,7 +218,7 @@ struct ArrStar {
 // Calls emit(slot, w) once per particle of U.  Returns 0, -PFEM_DEFER (a moment matrix the
 // Cholesky solve cannot factor, or more than UMAX distinct particles: queue the node for the
 // SVD pass) or, in the SVD pass, -PFEM_ERR_CAPACITY (more than UMAX_SVD distinct particles).
-constexpr int UMAX = 24;       // fast pass: jittered lattices have at most about 20
+constexpr int UMAX = PFEM_UMAX; // fast pass: jittered lattices have at most about 20
 constexpr int UMAX_SVD = 32;   // SVD pass (the stencil masks are 32-bit)
 
 // SVD = true (the FP64 pass over queued nodes): each edge's coefficients are the minimum-norm
@@ -222,14 +229,15 @@ constexpr int UMAX_SVD = 32;   // SVD pass (the stencil masks are 32-bit)
 // more than UM particles.
 template <int UM, typename R, typename SA>
 __device__ __forceinline__ int node_u_build(const int tri[3], const SA *st, const R lam[3],
-                                            int *us, R *uw, int &nu, unsigned vm[3], int vi[3])
+                                            int *us, R *uw, int &nu, unsigned vm[3], int vi[3],
+                                            int cap = UM)
 {
     nu = 0;
     bool over = false;
     auto add = [&](int s) -> int {
         for (int i = 0; i < nu; ++i)
             if (us[i] == s) return i;
-        if (nu == UM) { over = true; return 0; }
+        if (nu == cap) { over = true; return 0; }
         us[nu] = s;
         uw[nu] = R(0);
         return nu++;
@@ -248,9 +256,34 @@ __device__ __forceinline__ int node_u_build(const int tri[3], const SA *st, cons
     return over ? -1 : 0;
 }
 
+// node_u_build without the weights: the particle set and the stencil masks only.
+template <int UM, typename SA>
+__device__ __forceinline__ int node_u_sets(const int tri[3], const SA *st, int *us, int &nu,
+                                           unsigned vm[3], int vi[3], int cap = UM)
+{
+    nu = 0;
+    bool over = false;
+    auto add = [&](int s) -> int {
+        for (int i = 0; i < nu; ++i)
+            if (us[i] == s) return i;
+        if (nu == cap) { over = true; return 0; }
+        us[nu] = s;
+        return nu++;
+    };
+#pragma unroll
+    for (int e = 0; e < 3; ++e) vi[e] = add(tri[e]);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        unsigned m = 1u << vi[e];
+        for (int i = 0; i < st[e].n; ++i) m |= 1u << add(st[e][i]);
+        vm[e] = m;
+    }
+    return over ? -1 : 0;
+}
+
 // The three edge systems of a node over its particle set: uw[u] += 2 lambda_nu lambda_sg A_{u e}.
 // Returns 0, or -PFEM_DEFER when a moment matrix is below the fast-solve tolerance.
-template <typename P, typename R, typename S, bool REFINE, bool SVD, int UM>
+template <typename P, typename R, typename S, int REFINE, bool SVD, int UM>
 __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R> &np,
                                             const int *us, R *uw, const unsigned vm[3],
                                             const int vi[3], const R lam[3])
@@ -307,7 +340,33 @@ __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R
         const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
         S y[6];
         M.solve(b, y);
-        if (REFINE) {
+        if (REFINE == REFINE_FF) {
+            // r = b - sum_mu p_mu (p_mu . y) in float-float, with the monomials of the FP32
+            // offsets formed exactly (the same system the FP64 residual refines)
+            FF r[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r[k] = {(float)b[k], 0.f};
+            for (unsigned m = mask; m; m &= m - 1) {
+                const int i = __ffs(m) - 1;
+                S ox, oy;
+                offset(i, ox, oy);
+                const float X = (float)((ox - mx) * inv), Y = (float)((oy - my) * inv);
+                const FF p[6] = {{1.f, 0.f}, {X, 0.f}, {Y, 0.f}, ff_two_prod(X, X),
+                                 ff_two_prod(X, Y), ff_two_prod(Y, Y)};
+                FF t = {(float)y[0], 0.f};
+#pragma unroll
+                for (int k = 1; k < 6; ++k) t = ff_add(t, ff_mul(p[k], (float)y[k]));
+#pragma unroll
+                for (int k = 0; k < 6; ++k) r[k] = ff_add(r[k], ff_neg(ff_mul(p[k], t)));
+            }
+            S rs[6], dy[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rs[k] = (S)(r[k].h + r[k].l);
+            M.solve(rs, dy);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] += dy[k];
+        }
+        if (REFINE == REFINE_F64) {
             double r[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) r[k] = (double)b[k];
@@ -343,7 +402,7 @@ __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R
     return 0;
 }
 
-template <typename P, typename R, typename S, bool REFINE, bool SVD = false, typename SA,
+template <typename P, typename R, typename S, int REFINE, bool SVD = false, typename SA,
           typename Emit>
 __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P, R> &np,
                                               const int tri[3], const SA *st, const R lam[3],
@@ -355,7 +414,7 @@ __device__ __forceinline__ int node_quadratic(const P2MArgs &a, const NodePos<P,
     int nu;
     unsigned vm[3];
     int vi[3];
-    if (node_u_build<UM>(tri, st, lam, us, uw, nu, vm, vi) != 0)
+    if (node_u_build<UM>(tri, st, lam, us, uw, nu, vm, vi, SVD ? UM : min(a.ucap, UM)) != 0)
         return SVD ? -PFEM_ERR_CAPACITY : -PFEM_DEFER;
     const int r = node_u_solve<P, R, S, REFINE, SVD, UM>(a, np, us, uw, vm, vi, lam);
     if (r != 0) return r;
@@ -383,7 +442,7 @@ template <> __device__ __forceinline__ double nan_of<double>() { return __longlo
 
 // One mesh node.  WEIGHTS = false: write alpha_i for all C components; true: write the
 // node's distinct (slot, weight) pairs.
-template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS,
+template <typename P, typename V, typename R, typename S, int REFINE, int SHAPE, bool WEIGHTS,
           bool SVD = false>
 __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
 {
@@ -427,9 +486,9 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
                 for (int e = 0; e < 3; ++e) emit(tri[e], lam[e]);
             }
         }
-        st = defer_or_error(a, st, node);
+        st = defer_or_error(a, st, a.noff + node);
         if (st != 0) {
-            if (st < 0) record_error(a.status, -st, node);
+            if (st < 0) record_error(a.status, -st, a.noff + node);
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
         }
@@ -454,9 +513,9 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
             }
             if (over && st == 0) st = -PFEM_ERR_CAPACITY;
         }
-        st = defer_or_error(a, st, node);
+        st = defer_or_error(a, st, a.noff + node);
         if (st != 0) {
-            if (st < 0) record_error(a.status, -st, node);
+            if (st < 0) record_error(a.status, -st, a.noff + node);
             cnt = 0;
         }
         int *oi = a.w_idx + node * a.K;
@@ -475,7 +534,7 @@ __device__ __forceinline__ void p2m_node(const P2MArgs &a, int I, int J)
 #define PFEM_P2M_MIN_BLOCKS 12
 #endif
 
-template <typename P, typename V, typename R, typename S, bool REFINE, int SHAPE, bool WEIGHTS>
+template <typename P, typename V, typename R, typename S, int REFINE, int SHAPE, bool WEIGHTS>
 __global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m(P2MArgs a)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
@@ -484,9 +543,11 @@ __global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_p2m(P2MArgs a)
     p2m_node<P, V, R, S, REFINE, SHAPE, WEIGHTS>(a, I, J);
 }
 
-// The queued nodes again, in FP64 with the SVD solve of every edge, overwriting the fast pass's
-// placeholder output.  A node that fails here reports its error.
-template <typename P, typename V, typename R, bool WEIGHTS>
+// The queued nodes again, overwriting the fast pass's placeholder output: the geometry searched
+// per thread with the widest search radius (the launcher passes it in a.B.rmax), and with
+// quadratic shape functions every edge solved in FP64 by the SVD.  A node that fails here
+// reports its error.
+template <typename P, typename V, typename R, int SHAPE, bool WEIGHTS>
 __global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
 {
     const int cnt = min(*a.defer_count, a.defer_cap);
@@ -494,7 +555,7 @@ __global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
     f.defer_cap = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
         const long long node = a.defer_list[i];
-        p2m_node<P, V, R, double, false, PFEM_SHAPE_QUADRATIC, WEIGHTS, true>(
+        p2m_node<P, V, R, double, REFINE_NONE, SHAPE, WEIGHTS, true>(
             f, (int)(node % a.n), (int)(node / a.n));
     }
 }
@@ -536,30 +597,29 @@ inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r, bool wi
     return total;
 }
 
-// Resident 128-thread blocks per SM of the geometry kernel (sweep 12, 14, 16 on GB300: 14).
+// Resident 128-thread blocks per SM of the geometry kernel.
 #ifndef PFEM_GEOM_MIN_BLOCKS
-#define PFEM_GEOM_MIN_BLOCKS 14
+#define PFEM_GEOM_MIN_BLOCKS 8
 #endif
-// Node (I, J) of the mesh of a.n nodes per side: locate it, build its particle set and write
-// its record at index `rec` (node J * a.n + I of a single problem; the problem's offset plus
-// that in a batch, which also records the node's coordinates).
+// Node (I, J) of the mesh of a.n nodes per side: locate it and build its particle set from the
+// star table, and write its record at index `rec` (node J * a.n + I of a single problem; the
+// problem's offset plus that in a batch, which also records the node's coordinates).
 template <typename P, typename V, typename R>
-__device__ __forceinline__ void geom_node(const P2MArgs &a, const NodeRecs &r, int I, int J,
-                                          long long rec)
+__device__ __forceinline__ void geom_node(const P2MArgs &a, const StarTab &t, const NodeRecs &r,
+                                          int I, int J, long long rec)
 {
     const int nc = a.n - 1;
     const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
     const long long node = (long long)J * a.n + I;
     const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
     int tri[3];
-    int stars[3][KMAX];
-    int ns[3] = {0, 0, 0};
-    int st = locate(a.B, qn, a.R0, tri, stars[0], ns[0]);
-    for (int e = 0; e < 3 && st == 0; ++e)
-        if (ns[e] == 0) {
-            const int c = star_of(a.B, tri[e], a.R0, stars[e]);
-            if (c < 0) st = c;
-            else ns[e] = c;
+    int st = locate_tab(a.B, t, qn, a.R0, tri);
+    TabStar sa[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+        if (st == 0) {
+            sa[e] = tab_star(t, tri[e]);
+            if (sa[e].n < 0) st = sa[e].n == -1 ? -PFEM_FAR : sa[e].n;
         }
     int meta = -1;
     if (st == 0) {
@@ -568,12 +628,10 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const NodeRecs &r, i
         R lam[3];
         barycentric(a, np, tri, lam);
         int us[UMAX];
-        R uw[UMAX];
         int nu;
         unsigned vm[3];
         int vi[3];
-        const ArrStar sa[3] = {{stars[0], ns[0]}, {stars[1], ns[1]}, {stars[2], ns[2]}};
-        if (node_u_build<UMAX>(tri, sa, lam, us, uw, nu, vm, vi) != 0) {
+        if (node_u_sets<UMAX>(tri, sa, us, nu, vm, vi, min(a.ucap, UMAX)) != 0) {
             st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
         } else {
             for (int i = 0; i < nu; ++i) r.us[i * r.nodes + rec] = us[i];
@@ -588,8 +646,8 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const NodeRecs &r, i
     r.meta[rec] = meta;
     if (r.loc) r.loc[rec] = (long long)Iu | (long long)Ju << 21 | (long long)nc << 42;
     if (st != 0) {
-        st = defer_or_error(a, st, node);
-        if (st < 0) record_error(a.status, -st, node);
+        st = defer_or_error(a, st, rec);
+        if (st < 0) record_error(a.status, -st, rec);
         if (a.out) {                    // the adjoint uses this kernel without a mesh output
             R acc[8];
 #pragma unroll
@@ -600,12 +658,13 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const NodeRecs &r, i
 }
 
 template <typename P, typename V, typename R>
-__global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, NodeRecs r)
+__global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, StarTab t,
+                                                                        NodeRecs r)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
     if (I >= a.n || J >= a.n) return;
-    geom_node<P, V, R>(a, r, I, J, (long long)J * a.n + I);
+    geom_node<P, V, R>(a, t, r, I, J, (long long)J * a.n + I);
 }
 
 // Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
@@ -614,12 +673,12 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
 #ifndef PFEM_SOLVE_MIN_BLOCKS
 #define PFEM_SOLVE_MIN_BLOCKS 8
 #endif
-template <typename S, bool REFINE> constexpr int solve_min_blocks()
+template <typename S, int REFINE> constexpr int solve_min_blocks()
 {
-    return (sizeof(S) == 8 || REFINE) ? 4 : PFEM_SOLVE_MIN_BLOCKS;
+    return (sizeof(S) == 8 || REFINE != REFINE_NONE) ? 4 : PFEM_SOLVE_MIN_BLOCKS;
 }
 
-template <typename P, typename V, typename R, typename S, bool REFINE>
+template <typename P, typename V, typename R, typename S, int REFINE>
 __global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solve(P2MArgs a, NodeRecs r)
 {
     const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -1,0 +1,62 @@
+// stars.cu -- the star table (startab.cuh): the Delaunay star of every particle, one thread per
+// particle, then the particles whose list attempt failed by a region search.
+#include <algorithm>
+
+#include "internal.h"
+#include "startab.cuh"
+
+namespace pfem {
+
+__global__ void __launch_bounds__(STAR_TPB) k_star_list(Bins B, int R0, StarTab t, DevStatus *st)
+{
+    __shared__ float2 sxy[STAR_KL * STAR_TPB];
+    __shared__ int ss[STAR_KL * STAR_TPB];
+    const long long v = blockIdx.x * (long long)STAR_TPB + threadIdx.x;
+    if (v >= t.N) return;
+    SmemList L{sxy + threadIdx.x, ss + threadIdx.x, STAR_TPB};
+    star_list_slot(B, R0, t, v, L, st);
+}
+
+// The queued particles, with the radius of B (the launcher passes the widest one).
+__global__ void __launch_bounds__(64) k_star_retry(Bins B, int R0, StarTab t, DevStatus *st)
+{
+    const int n = min(*t.qcount, (int)min(t.N, (long long)0x7fffffff));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        star_retry_slot(B, R0, t, t.queue[i], st);
+}
+
+size_t star_tab_bytes(long long N)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t n = (size_t)(N > 0 ? N : 1);
+    return al(n * KMAX * sizeof(int)) + al(n * sizeof(int)) + al(n * sizeof(int));
+}
+
+StarTab star_tab_layout(char *base, long long N, int *qcount)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t n = (size_t)(N > 0 ? N : 1);
+    StarTab t;
+    t.nbr = (int *)base;
+    t.cnt = (int *)(base + al(n * KMAX * sizeof(int)));
+    t.queue = (int *)(base + al(n * KMAX * sizeof(int)) + al(n * sizeof(int)));
+    t.qcount = qcount;
+    t.N = N;
+    return t;
+}
+
+cudaError_t launch_star_table(const Bins &B, int R0, int rmax_far, const StarTab &t,
+                              DevStatus *st, cudaStream_t s)
+{
+    if (t.N <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(t.qcount, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_star_list<<<(unsigned)((t.N + STAR_TPB - 1) / STAR_TPB), STAR_TPB, 0, s>>>(B, R0, t, st);
+    Bins Bf = B;
+    Bf.rmax = std::max(B.rmax, rmax_far);
+    k_star_retry<<<num_sms() * 4, 64, 0, s>>>(Bf, R0, t, st);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+}  // namespace pfem

@@ -13,7 +13,6 @@ from typing import Callable, Dict, Iterable, List, Tuple
 import torch
 
 _CACHE: Dict[tuple, dict] = {}
-SMS = 152
 
 
 def time_ms(fn: Callable[[], None], reps: int = 3, warmup: int = 1) -> float:
@@ -44,6 +43,7 @@ def tune_batch(batch, pos, vals, shape, solve=None, reps: int = 3, quick: bool =
         batch.config.update({k: v for k, v in _CACHE[key].items() if not k.startswith("_")})
         return _CACHE[key]
     batch.build(pos)
+    SMS = torch.cuda.get_device_properties(batch.device).multi_processor_count
     rows = (8,) if quick else (4, 8, 16)
     mult = (4, 8) if quick else (2, 4, 8, 16)
     p2m_cands = [{"tile_rows": r, "p2m_blocks": SMS * m} for r, m in itertools.product(rows, mult)]

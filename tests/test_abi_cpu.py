@@ -36,7 +36,7 @@ def test_binding_covers_header():
 
 
 def test_host_queries(lib):
-    assert lib.pfem_abi_version() == 1
+    assert lib.pfem_abi_version() == 2
     assert lib.pfem_status_string(4) == b"capacity exceeded"
     assert lib.pfem_default_bins(1025, 2048 * 2048) == 1024
     assert lib.pfem_default_bins(33, 4096) == 32
@@ -48,29 +48,72 @@ def test_host_queries(lib):
 def test_bad_arguments_are_rejected_on_host(lib):
     null = ctypes.c_void_p(0)
     # n too small / C out of range / NULL buffers: PFEM_ERR_INVALID_ARG, nothing launched
-    assert lib.pfem_interp_m2p(5, 10, null, 0, 1, null, null, 0, null) == 1
-    assert lib.pfem_interp_m2p(33, 10, null, 0, 9, null, null, 0, null) == 1
-    assert lib.pfem_project_p2m(33, 32, 4096, null, 0, null, null, null, 1, null, 0, 1, 0, null,
-                                null, 0, 0, null, null, 0, null) == 1
-    assert lib.pfem_build_cells(0, 10, null, 0, null, null, null, null, null, 0, null) == 1
+    assert lib.pfem_interp_m2p(null, 5, 10, null, 0, 1, null, null, 0, null) == 1
+    assert b"out of range" in lib.pfem_last_error(null)
+    assert lib.pfem_interp_m2p(null, 33, 10, null, 0, 9, null, null, 0, null) == 1
+    assert lib.pfem_project_p2m(null, 33, 32, 4096, null, 0, null, null, null, 1, null, 0, 1, 0,
+                                null, null, 0, 0, null, null, 0, null) == 1
+    assert b"NULL" in lib.pfem_last_error(null)
+    assert lib.pfem_build_cells(null, 0, 10, null, 0, null, null, null, null, null, 0, null) == 1
     # workspace too small
     fake = ctypes.c_void_p(1 << 20)
-    assert lib.pfem_build_cells(8, 100, fake, 0, fake, fake, fake, fake, fake, 16, null) == 3
+    assert lib.pfem_build_cells(null, 8, 100, fake, 0, fake, fake, fake, fake, fake, 16, null) == 3
+    assert b"ws_bytes" in lib.pfem_last_error(null)
     assert lib.pfem_read_status(null, None, None, null) == 1
 
 
+def test_context_options_and_last_error(lib):
+    """pfem_create / pfem_get_options / pfem_last_error / pfem_destroy on the host: defaults are
+    filled in, out-of-range options are refused with a message, and a context keeps the error
+    text of the calls made with it (separately from calls without a context)."""
+    import paper_1610_05266_gb300._lib as L
+    d = L.Options()
+    lib.pfem_options_default(ctypes.byref(d))
+    assert (d.walk_max_steps, d.star_capacity, d.node_capacity, d.batch_tile_rows) == (64, 16, 24, 8)
+    h = ctypes.c_void_p()
+    bad = L.Options(star_capacity=2)
+    assert lib.pfem_create(ctypes.byref(h), ctypes.byref(bad)) == 1
+    assert not h.value and b"star_capacity" in lib.pfem_last_error(None)
+    bad = L.Options(batch_tile_rows=5)
+    assert lib.pfem_create(ctypes.byref(h), ctypes.byref(bad)) == 1
+    opt = L.Options(walk_max_steps=-1, star_capacity=3, search_radius_max=2)
+    assert lib.pfem_create(ctypes.byref(h), ctypes.byref(opt)) == 0 and h.value
+    got = L.Options()
+    assert lib.pfem_get_options(h, ctypes.byref(got)) == 0
+    assert (got.walk_max_steps, got.star_capacity, got.node_capacity, got.search_radius_max) == (-1, 3, 24, 2)
+    null = ctypes.c_void_p(0)
+    assert lib.pfem_interp_m2p(h, 9, 10, null, 0, 0, null, null, 0, null) == 1
+    assert b"C = 0" in lib.pfem_last_error(h)
+    lib.pfem_interp_m2p(null, 9, 10, null, 0, 1, null, null, 5, null)
+    assert b"C = 0" in lib.pfem_last_error(h)               # the context's text is its own
+    lib.pfem_destroy(h)
+    lib.pfem_destroy(null)
+
+
+def test_python_context_wrapper():
+    import paper_1610_05266_gb300 as P
+    ctx = P.Context(walk_max_steps=3, star_capacity=5)
+    o = ctx.options()
+    assert o["walk_max_steps"] == 3 and o["star_capacity"] == 5 and o["node_capacity"] == 24
+    with pytest.raises(P.PfemError) as e:
+        P.Context(node_capacity=99)
+    assert "node_capacity" in str(e.value)
+
+
 def test_workspace_sizes_cover_queue_and_records(lib):
-    """Quadratic P2M keeps an SVD-pass queue (8 bytes per node after byte 512) and 136 bytes of
-    node record per node in the workspace; pfem_workspace_size covers both even when the
-    binning scratch is small (few particles on a fine mesh).  The batched workspace covers the
-    records plus an 8-byte node key per node when given the node total, and is the binning
-    scratch alone without it."""
+    """P2M keeps in the workspace a fix-pass queue (8 bytes per node after byte 512), 136 bytes
+    of node record per node and the star table (64 + 8 bytes per particle); pfem_workspace_size
+    covers them even when the binning scratch is small (few particles on a fine mesh).  The
+    batched workspace covers the queue, the records plus an 8-byte node key per node and the
+    star table when given the node total, and is the binning scratch alone without it."""
     n = 1025
     rec = 4 + 12 + 24 + 24 * 4
-    assert lib.pfem_workspace_size(n, 32, 4096, 4) >= 512 + 8 * n * n + rec * n * n
-    assert lib.pfem_workspace_size(n, 1024, 2048 * 2048, 4) >= 512 + 8 * n * n + rec * n * n
+    tab = 64 + 8
+    N = 2048 * 2048
+    assert lib.pfem_workspace_size(n, 32, 4096, 4) >= 512 + 8 * n * n + rec * n * n + tab * 4096
+    assert lib.pfem_workspace_size(n, 1024, N, 4) >= 512 + 8 * n * n + rec * n * n + tab * N
     nodes = 27_000_000
-    assert lib.pfem_batch_workspace_size(10**6, 250_000, nodes) >= 256 + (rec + 8) * nodes
+    assert lib.pfem_batch_workspace_size(10**6, 250_000, nodes) >= 256 + (8 + rec + 8) * nodes + tab * 10**6
     bins_only = lib.pfem_batch_workspace_size(10**6, 250_000, 0)
     assert bins_only >= 4 * (250_000 + 1) + 8 * 10**6
     assert bins_only < 256 + (rec + 8) * nodes

@@ -420,13 +420,16 @@ def test_ill_conditioned_nodes_take_the_svd_pass(P):
     assert np.abs(mesh_w.cpu().numpy().astype(np.float64) - ref).max() <= 1e-5 * vmax
 
 
-@pytest.mark.parametrize("solve", ["f32", "f32ref"])
+@pytest.mark.parametrize("solve", ["f32", "f32ref", "f32ff", "f64"])
 def test_fused_and_split_fast_pass_agree(P, solve):
-    """With a workspace of 512 bytes (status only: no queue, no node records) the quadratic
-    P2M runs its fast pass as one fused kernel; with the full workspace, as the geometry and
-    solve kernels.  Same arithmetic in the same order: bit-identical meshes, no device error."""
+    """With a workspace of 512 bytes (status only: no queue, no star table, no node records)
+    the quadratic P2M runs its fast pass as one fused kernel that searches every node's stars;
+    with the full workspace, as the star table, the geometry kernel and the solve kernel.  Same
+    topology (exact predicates) and the same arithmetic in the same order: bit-identical
+    meshes, no device error, for every solve variant."""
     from paper_1610_05266_gb300 import api
-    sv = {"f32": P.PFEM_SOLVE_F32, "f32ref": P.PFEM_SOLVE_F32_REFINED}[solve]
+    sv = {"f32": P.PFEM_SOLVE_F32, "f32ref": P.PFEM_SOLVE_F32_REFINED,
+          "f32ff": P.PFEM_SOLVE_F32_REFINED_FF, "f64": P.PFEM_SOLVE_F64}[solve]
     pr = G.scaled_config("tgz", 129, 256)
     proj, _ = gpu_setup(P, pr, torch.float32)
     v = torch.tensor(pr.vals, dtype=torch.float32, device="cuda")
