@@ -139,7 +139,7 @@ const char *pfem_status_string(pfem_status s);
 int32_t pfem_default_bins(int32_t n, int64_t N);
 
 /* Bytes of workspace `ws` needed by the calls below for these sizes (>= 256); with n > 0 it
- * includes room for the quadratic P2M queue of every node (see pfem_project_p2m). */
+ * includes the fix-pass queue, node records and star table of pfem_project_p2m. */
 size_t pfem_workspace_size(int32_t n, int32_t nb, int64_t N, int32_t C);
 
 /* Status word recorded by device code in `ws` since the last reset; synchronises `stream`
@@ -186,9 +186,12 @@ pfem_status pfem_build_cells_noalloc(int32_t nb, int64_t N, const void *pos, pfe
                                      uint32_t *q_sorted, void *stream);
 
 /* Delaunay stars (App. B: neighbours = particles joined by a Delaunay edge) of every
- * particle, counter-clockwise, in slot indices: nbrs [N, PFEM_KMAX] int32 (unused entries
- * -1), counts [N] int32.  Diagnostic entry point; the projections compute the stars they
- * need on the fly. */
+ * particle, counter-clockwise from its nearest neighbour, in slot indices: nbrs [N, PFEM_KMAX]
+ * int32 (unused entries -1), counts [N] int32 (0 for a star that failed; its error is in the
+ * status word).  This is the star table the quadratic projections build for themselves: one
+ * thread per particle computes the convex hull of the particle's neighbours within two mean
+ * spacings inverted about it, and the particles whose hull cannot be certified are searched
+ * again over growing regions.  ws holds at least 256 + 4 N bytes (the retry queue). */
 pfem_status pfem_delaunay_stars(pfem_ctx *ctx, int32_t nb, int64_t N, const uint32_t *q_sorted,
                                 const int32_t *cell_start, int32_t *nbrs, int32_t *counts,
                                 void *ws, size_t ws_bytes, void *stream);
@@ -214,16 +217,22 @@ pfem_status pfem_shape_quadratic(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N
  *   mesh_vals [n, n, C] val_t out
  * C in 1..8.
  * Quadratic shape functions: each edge's coefficient system (App. B) is solved by a Cholesky
- * factorisation of its 6x6 moment matrix.  A node with an edge whose pivot falls below the
+ * factorisation of its 6x6 moment matrix.  The call runs a fast pass over every node and a fix
+ * pass over the nodes the fast pass queued: a node with an edge whose pivot falls below the
  * fast tolerance (rank deficient, e.g. a stencil of five particles, or too ill-conditioned for
- * the precision: 3e-4 of the trace in FP32, 1e-6 in FP64), or with more than 24 distinct
- * particles, is queued and recomputed in FP64 with the minimum-norm least-squares solution by
- * SVD (App. A), by a further kernel on the same stream.  The queue uses the workspace after
- * its first 512 bytes (8 bytes per queued node, at most n*n): with ws_bytes < 520 there is no
- * queue and such nodes record PFEM_ERR_DEGENERATE (PFEM_ERR_CAPACITY when the queue is full).
- * With FP32 solves and room after the queue for 136 bytes of record per node, the fast pass
- * runs as a geometry kernel and a solve kernel handing over those records; with less, as one
- * fused kernel (same results).  The workspace of pfem_workspace_size() has room for both. */
+ * the precision: 3e-4 of the trace in FP32, 1e-6 in FP64), with more than the context's
+ * node_capacity distinct particles, or whose search ran out of its first region (a sparse
+ * region or a void), is recomputed in FP64 with the minimum-norm least-squares solution by SVD
+ * (App. A) and searches up to the context's search_radius_max.  Linear shape functions queue
+ * only the last kind.  Workspace layout after the 256-byte status block: the fix-pass queue
+ * from byte 512 (8 bytes per node; with ws_bytes < 520 there is no queue and such nodes record
+ * PFEM_ERR_DEGENERATE or PFEM_ERR_CAPACITY), then, for the quadratic apply form, 136 bytes of
+ * record per node and the star table (72 bytes per particle).  With room for them the fast
+ * pass is the star table of every particle (see pfem_delaunay_stars), a per-node geometry
+ * kernel that locates the node and builds its particle set from the table, and a solve kernel
+ * for the three edge systems and the weights; with less, one kernel searches every node's
+ * stars itself (same results, slower).  The workspace of pfem_workspace_size() has room for
+ * everything. */
 pfem_status pfem_project_p2m(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                              pfem_dtype pos_t, const uint32_t *q_sorted,
                              const int32_t *cell_start, const int32_t *perm, int32_t C,

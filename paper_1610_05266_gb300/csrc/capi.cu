@@ -336,7 +336,8 @@ pfem_status pfem_delaunay_stars(pfem_ctx *ctx, int32_t nb, int64_t N, const uint
     pfem_status st = make_geo(ctx, fn, 9, nb, N, q_sorted, PFEM_F32, q_sorted, cell_start, &g);
     if (st != PFEM_OK) return st;
     if (!nbrs || !counts || !ws) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: NULL buffer", fn);
-    if (ws_bytes < 256) return say(ctx, PFEM_ERR_WORKSPACE, "%s: ws_bytes < 256", fn);
+    if (ws_bytes < stars_ws_bytes(N))
+        return say(ctx, PFEM_ERR_WORKSPACE, "%s: ws_bytes = %zu < %zu", fn, ws_bytes, stars_ws_bytes(N));
     return cuda_result(ctx, launch_stars(g, nbrs, counts, (DevStatus *)ws, (cudaStream_t)stream), fn);
 }
 

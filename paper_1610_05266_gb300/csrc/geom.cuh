@@ -68,13 +68,22 @@ __device__ __forceinline__ Region make_region(const Bins &B, uint2 p, int R)
 {
     Region g;
     g.R = R;
-    g.bx = bin_of(p.x, B.nb);
-    g.by = bin_of(p.y, B.nb);
-    const long long bw = (long long)((1ull << 32) / (unsigned long long)B.nb);
-    g.cl_lo_x = (float)((long long)p.x - bin_lo(g.bx, B.nb) + R * bw);
-    g.cl_hi_x = (float)(bin_lo(g.bx + 1, B.nb) - 1 - (long long)p.x + R * bw);
-    g.cl_lo_y = (float)((long long)p.y - bin_lo(g.by, B.nb) + R * bw);
-    g.cl_hi_y = (float)(bin_lo(g.by + 1, B.nb) - 1 - (long long)p.y + R * bw);
+    // q * nb = b * 2^32 + f: bin b, and p lies f / nb fixed-point units past the bin's real
+    // left edge (b * 2^32 / nb).  The integer bin boundaries are within one unit of the real
+    // ones, so the clearances below, reduced by a relative 2^-20 and 4 units for the FP32
+    // rounding, are lower bounds of the exact ones.
+    const float inv = __frcp_rn((float)B.nb);
+    const float w = 4294967296.0f * inv;
+    const unsigned long long mx = (unsigned long long)p.x * (unsigned)B.nb;
+    const unsigned long long my = (unsigned long long)p.y * (unsigned)B.nb;
+    g.bx = (int)(mx >> 32);
+    g.by = (int)(my >> 32);
+    const float lx = (float)(unsigned)mx * inv, ly = (float)(unsigned)my * inv;
+    const float Rw = (float)R * w, s = 1.0f - 9.5367431640625e-07f;
+    g.cl_lo_x = fmaf(lx + Rw, s, -4.f);
+    g.cl_hi_x = fmaf((w - lx) + Rw, s, -4.f);
+    g.cl_lo_y = fmaf(ly + Rw, s, -4.f);
+    g.cl_hi_y = fmaf((w - ly) + Rw, s, -4.f);
     return g;
 }
 

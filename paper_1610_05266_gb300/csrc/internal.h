@@ -85,6 +85,7 @@ cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_d
                          const int *w_idx, const void *w, int K, pfem_dtype w_t, void *out,
                          cudaStream_t s);
 cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st, cudaStream_t s);
+size_t stars_ws_bytes(long long N);
 cudaError_t launch_m2p_quadratic(int n, long long N, const void *pos, pfem_dtype pos_t, int C,
                                  const void *mesh, void *vals, pfem_dtype val_t, cudaStream_t s);
 cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, int C,

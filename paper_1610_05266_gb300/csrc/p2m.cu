@@ -222,27 +222,36 @@ cudaError_t launch_apply(int n, const int *perm, int C, const void *vals, pfem_d
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(128, PFEM_P2M_MIN_BLOCKS) k_stars(Bins B, int R0, long long N, int *nbrs, int *counts,
-                                               DevStatus *st)
+// The star table written straight into the caller's arrays, then padded: unused entries -1 and
+// a failed star's count 0 (its error is in the status word).
+__global__ void k_stars_pad(long long N, int *nbrs, int *counts)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
-        int loc[KMAX];
-        const int c = star_of(B, (int)v, R0, loc);
-        if (c < 0) record_error(st, -c, v);
-        const int cnt = c < 0 ? 0 : c;
-        for (int k = 0; k < KMAX; ++k) nbrs[v * KMAX + k] = k < cnt ? loc[k] : -1;
-        counts[v] = cnt;
+        const int c = counts[v] < 0 ? 0 : counts[v];
+        for (int k = c; k < KMAX; ++k) nbrs[v * KMAX + k] = -1;
+        counts[v] = c;
     }
 }
+
+// Workspace bytes of pfem_delaunay_stars: the status block and the retry queue.
+size_t stars_ws_bytes(long long N) { return 256 + 4 * (size_t)(N > 0 ? N : 1); }
 
 cudaError_t launch_stars(const GeoArgs &g, int *nbrs, int *counts, DevStatus *st, cudaStream_t s)
 {
     P2MArgs a = make_args(g, st);
-    long long blocks = (g.N + 127) / 128;
-    if (blocks > num_sms() * 32LL) blocks = num_sms() * 32LL;
+    StarTab t;
+    t.nbr = nbrs;
+    t.cnt = counts;
+    t.queue = (int *)((char *)st + 256);
+    t.qcount = (int *)((char *)st + 64);
+    t.N = g.N;
+    cudaError_t e = launch_star_table(a.B, g.R0, g.rmax_far, t, st, s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (g.N + 255) / 256;
+    if (blocks > num_sms() * 16LL) blocks = num_sms() * 16LL;
     if (blocks < 1) blocks = 1;
-    k_stars<<<(unsigned)blocks, 128, 0, s>>>(a.B, g.R0, g.N, nbrs, counts, st);
+    k_stars_pad<<<(unsigned)blocks, 256, 0, s>>>(g.N, nbrs, counts);
     count_launch();
     return cudaGetLastError();
 }

@@ -61,26 +61,187 @@ static __device__ __noinline__ int locate_tab(const Bins &B, const StarTab &t, u
     return fan_walk(B, p, v0, s0, s0.n, [&](int u, int w) { return tab_apex(t, u, w); }, tri);
 }
 
-// Threads per block and candidate-list capacity of the list kernels.  The list lives in shared
-// memory, one column per thread (20 x 12 bytes x 128 threads = 30 KB per block, 7 blocks per SM).
+// Threads per block and candidate-list capacity of the list kernels.  The lists live in shared
+// memory, one column per thread (18 candidates x 17 bytes x 128 threads = 39 KB per block).
 // Jittered lattices have at most 17 particles within the 2-spacing cutoff; longer lists go to the
 // retry kernel.
 constexpr int STAR_TPB = 128;
 #ifndef PFEM_STAR_KL
-#define PFEM_STAR_KL 20
+#define PFEM_STAR_KL 18
 #endif
 constexpr int STAR_KL = PFEM_STAR_KL;
 
+// A thread's candidate list for the hull star: coordinates relative to v (FP32), angular key,
+// slot, and the hull stack (list indices); entry k of thread t at k * stride + t.
+struct HullList {
+    float2 *xy;
+    float *key;
+    int *s;
+    unsigned char *stk;
+    int stride;
+};
+
+// Pseudo-angle of (x, y) in [0, 4): monotone in the polar angle (0 along +x, 1 along +y, ...).
+__device__ __forceinline__ float pseudo_angle(float x, float y)
+{
+    const float p = __fdividef(y, fabsf(x) + fabsf(y));
+    return x >= 0.f ? (y >= 0.f ? p : 4.f + p) : 2.f - p;
+}
+
+// Keys closer than this may be out of order after FP32 rounding (their error is below 1e-6):
+// such pairs are ordered exactly.
+constexpr float KEY_EPS = 4e-6f;
+
+// The Delaunay star of v from the candidates within distance D (capacity KLC), by the convex
+// hull of the candidates inverted about v.  Inversion c -> c/|c|^2 maps the circles through v
+// to lines, so an empty circle through v, a, b becomes a hull edge between the images of a
+// and b; and the orientation of three images is the sign of the lifted incircle determinant of
+// (v, a, b, c) -- the predicate of the gift-wrapping search, with the same tie-break.  So the
+// hull's vertices in counter-clockwise order are v's star.  Steps: gather the candidates (the
+// nearest one, u0, is always a Delaunay neighbour), sort them by angle about v starting at u0,
+// one Graham scan, then certify every triangle (v, w_j, w_j+1) exactly as the gift-wrapping
+// search does (the circumcircle inside the searched region and within D of v).  Returns the
+// count, -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
+template <int KLC, typename Out>
+__device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const Region &g, float D,
+                                         const HullList &L, Out &&out)
+{
+    const int S = L.stride;
+    int cnt = 0, u0 = -1, s0 = 0x7fffffff;
+    long long d2b = 0x7fffffffffffffffLL;
+    float lb = 3.4e38f;
+    bool dup = false, over = false;
+    const float D2 = D * D;
+    for_region(B, g, [&](int s) {
+        if (s == v) return;
+        const int2 d = rel(__ldg(B.q + s), pv);
+        const float fx = (float)d.x, fy = (float)d.y;
+        const float l = fmaf(fx, fx, fy * fy);
+        if (l > D2) return;
+        dup |= (d.x | d.y) == 0;
+        if (cnt == KLC) { over = true; return; }
+        L.xy[cnt * S] = make_float2(fx, fy);
+        L.s[cnt * S] = s;
+        if (l <= lb * 1.000001f) {             // near the nearest so far: decide exactly
+            const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
+            if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; lb = l; }
+        }
+        ++cnt;
+    });
+    if (dup) return -PFEM_ERR_DEGENERATE;
+    if (over || u0 < 0) return -1;
+    auto exact_of = [&](int slot) { return rel(__ldg(B.q + slot), pv); };
+    // angular keys relative to u0's direction (u0 first); candidates on u0's ray lie farther
+    // than u0 and cannot be neighbours: they are dropped (key +inf, sorted last)
+    const float2 U = L.xy[u0 * S];
+    const float ku = pseudo_angle(U.x, U.y);
+    const int2 du = exact_of(s0);
+    int live = 0;
+    for (int k = 0; k < cnt; ++k) {
+        float key = -1.f;
+        if (k != u0) {
+            const float2 c = L.xy[k * S];
+            key = pseudo_angle(c.x, c.y) - ku;
+            if (key < 0.f) key += 4.f;
+            if (key < KEY_EPS || key > 4.f - KEY_EPS) {          // near u0's ray: exactly
+                const int2 dc = exact_of(L.s[k * S]);
+                const long long cr = cross(du, dc);
+                if (cr > 0) key = key < 2.f ? key : 0.f;          // just counter-clockwise
+                else if (cr < 0) key = key > 2.f ? key : 4.f;     // just clockwise: last
+                else key = 3.4e38f;                               // on u0's ray
+            }
+        }
+        live += key < 1e30f;
+        L.key[k * S] = key;
+    }
+    // Should entry (kj, sj) come after (kc, sc)?  Near-equal keys are ordered by the exact cross
+    // product; on one ray the farther particle comes first (its image lies inside the hull and
+    // the scan removes it).
+    auto after = [&](float kj, int sj, float kc, int sc) -> bool {
+        if (kj - kc > KEY_EPS) return true;
+        if (kc - kj > KEY_EPS) return false;
+        if (kj > 1e30f || kc > 1e30f) return kj > kc;
+        const int2 dj = exact_of(sj), dc = exact_of(sc);
+        const long long cr = cross(dj, dc);
+        if (cr != 0) return cr < 0;
+        return (long long)dj.x * dj.x + (long long)dj.y * dj.y <
+               (long long)dc.x * dc.x + (long long)dc.y * dc.y;
+    };
+    for (int i = 1; i < cnt; ++i) {
+        const float2 c = L.xy[i * S];
+        const float kc = L.key[i * S];
+        const int sc = L.s[i * S];
+        int j = i - 1;
+        for (; j >= 0; --j) {
+            const float kj = L.key[j * S];
+            const int sj = L.s[j * S];
+            if (!after(kj, sj, kc, sc)) break;
+            L.xy[(j + 1) * S] = L.xy[j * S];
+            L.key[(j + 1) * S] = kj;
+            L.s[(j + 1) * S] = sj;
+        }
+        L.xy[(j + 1) * S] = c;
+        L.key[(j + 1) * S] = kc;
+        L.s[(j + 1) * S] = sc;
+    }
+    // Graham scan from u0 (now entry 0) over the live entries
+    auto left = [&](int a, int b, int c) -> bool {
+        const float2 A = L.xy[a * S], Bp = L.xy[b * S], Cp = L.xy[c * S];
+        const float la = fmaf(A.x, A.x, A.y * A.y), lbb = fmaf(Bp.x, Bp.x, Bp.y * Bp.y),
+                    lc = fmaf(Cp.x, Cp.x, Cp.y * Cp.y);
+        const float bc = fmaf(Bp.x, Cp.y, -Bp.y * Cp.x), ac = fmaf(A.x, Cp.y, -A.y * Cp.x),
+                    ab = fmaf(A.x, Bp.y, -A.y * Bp.x);
+        const float det = fmaf(la, bc, fmaf(-lbb, ac, lc * ab));
+        const float ra = sqrtf(la), rb = sqrtf(lbb), rc = sqrtf(lc);
+        const float mag = ra * rb * rc * (ra + rb + rc);
+        const float bnd = 1.9073486328125e-06f * mag;
+        if (det > bnd) return true;
+        if (det < -bnd) return false;
+        const int sa = L.s[a * S], sb = L.s[b * S], sc = L.s[c * S];
+        const uint2 qa = __ldg(B.q + sa), qb = __ldg(B.q + sb), qc = __ldg(B.q + sc);
+        return incircle_exact(rel(qa, pv), rel(qb, pv), rel(qc, pv), pv, qa, qb, qc) < 0;
+    };
+    int sp = 0;
+    L.stk[0] = 0;
+    sp = 1;
+    for (int i = 1; i < live; ++i) {
+        while (sp >= 2 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], i)) --sp;
+        L.stk[sp * S] = (unsigned char)i;
+        ++sp;
+    }
+    while (sp >= 3 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], 0)) --sp;
+    if (sp < 3) return -1;
+    // certify every triangle (v, w_j, w_j+1): counter-clockwise, circumcircle inside the region
+    // and within D of v (then no particle outside the list can lie inside it)
+    const float clx = g.cl_lo_x, chx = g.cl_hi_x, cly = g.cl_lo_y, chy = g.cl_hi_y;
+    for (int j = 0; j < sp; ++j) {
+        const float2 a = L.xy[L.stk[j * S] * S];
+        const float2 b = L.xy[L.stk[(j + 1 == sp ? 0 : j + 1) * S] * S];
+        const FCirc cb = make_fcirc(a.x, a.y, b.x, b.y);
+        if (!(cb.K > 1e-3f * cb.Ka)) return -1;
+        const float inv2k = 0.5f / cb.K;
+        const float ccx = -cb.P * inv2k, ccy = -cb.Q * inv2k;
+        const float r = sqrtf(fmaf(ccx, ccx, ccy * ccy));
+        const float err = 1e-4f * (cb.Pa + cb.Qa + (fabsf(cb.P) + fabsf(cb.Q)) * cb.Ka / cb.K) / cb.K + 64.f;
+        const float ext = r + err;
+        if (ccx - ext < -clx || ccx + ext > chx || ccy - ext < -cly || ccy + ext > chy) return -1;
+        if (2.f * ext > D * 0.9999f) return -1;
+    }
+    if (sp > B.kcap) return -PFEM_ERR_CAPACITY;
+    for (int j = 0; j < sp; ++j) out(j, L.s[L.stk[j * S] * S]);
+    return sp;
+}
+
 // The list attempt for slot v (candidates in L): its star into the table, or v queued.
 __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const StarTab &t, long long v,
-                                               SmemList &L, DevStatus *st)
+                                               const HullList &L, DevStatus *st)
 {
     const uint2 pv = __ldg(B.q + v);
     int *out = t.nbr + v * KMAX;
     int c = -1;
     if (B.dmax > 0.f)
-        c = star_list_into<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
-                                    [&](int k, int s) { out[k] = s; });
+        c = star_hull<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
+                               [&](int k, int s) { out[k] = s; });
     if (c == -1) {
         t.cnt[v] = -1;
         t.queue[atomicAdd(t.qcount, 1)] = (int)v;   // at most N entries: each slot once

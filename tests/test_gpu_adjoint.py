@@ -48,8 +48,10 @@ def test_p2m_backward_fp64_matches_oracle(P, small, shape):
     code, _ = proj.backward_status()
     assert code == 0
     ov, op = O.p2m_backward(n, pos, vals, g, shape=shape)
-    assert relerr(gv.cpu().numpy(), ov) <= 1e-12
-    assert relerr(gp.cpu().numpy(), op) <= 1e-10
+    ev, ep = relerr(gv.cpu().numpy(), ov), relerr(gp.cpu().numpy(), op)
+    print(f"FP64 P2M adjoint vs oracle (shape {shape}): values {ev:.2e}, positions {ep:.2e}")
+    assert ev <= 1e-12
+    assert ep <= 1e-12
 
 
 def test_checkpoint_equals_recompute(P, small):
@@ -178,5 +180,5 @@ def test_gradient_workload_full_size_band(P):
         assert code == 0
         res[str(dt)] = (relerr(gv.cpu().numpy(), ov), relerr(gp.cpu().numpy(), op))
     print("full-size band gradient error (vals, pos):", res)
-    assert res["torch.float64"][0] <= 1e-12 and res["torch.float64"][1] <= 1e-9
+    assert res["torch.float64"][0] <= 1e-12 and res["torch.float64"][1] <= 1e-12
     assert res["torch.float32"][0] < 1e-5 and res["torch.float32"][1] < 1e-2
