@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(BSTAR) k_star_list_batch(const BPlanDev *pl, P
     __shared__ float2 sxy[STAR_KL * BSTAR];
     __shared__ float skey[STAR_KL * BSTAR];
     __shared__ int ss[STAR_KL * BSTAR];
+    __shared__ unsigned char sord[STAR_KL * BSTAR];
     __shared__ unsigned char sstk[STAR_KL * BSTAR];
     if (!totals_ok(pl, nullptr, &t, base.status)) return;
     const long long *sp = plan_star_tiles(pl);
@@ -193,7 +194,8 @@ __global__ void __launch_bounds__(BSTAR) k_star_list_batch(const BPlanDev *pl, P
         if (i >= d.N) continue;
         P2MArgs a;
         problem_args(a, base, d);
-        const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sstk + threadIdx.x, BSTAR};
+        const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sord + threadIdx.x,
+                      sstk + threadIdx.x, BSTAR};
         star_list_slot(a.B, a.R0, t, d.poff + i, L, a.status);
     }
 }

@@ -12,10 +12,12 @@ __global__ void __launch_bounds__(STAR_TPB) k_star_list(Bins B, int R0, StarTab 
     __shared__ float2 sxy[STAR_KL * STAR_TPB];
     __shared__ float skey[STAR_KL * STAR_TPB];
     __shared__ int ss[STAR_KL * STAR_TPB];
+    __shared__ unsigned char sord[STAR_KL * STAR_TPB];
     __shared__ unsigned char sstk[STAR_KL * STAR_TPB];
     const long long v = blockIdx.x * (long long)STAR_TPB + threadIdx.x;
     if (v >= t.N) return;
-    const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sstk + threadIdx.x, STAR_TPB};
+    const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sord + threadIdx.x,
+                      sstk + threadIdx.x, STAR_TPB};
     star_list_slot(B, R0, t, v, L, st);
 }
 

@@ -71,17 +71,20 @@ constexpr int STAR_TPB = 128;
 #endif
 constexpr int STAR_KL = PFEM_STAR_KL;
 
-// A thread's candidate list for the hull star: coordinates relative to v (FP32), angular key,
-// slot, and the hull stack (list indices); entry k of thread t at k * stride + t.
+// A thread's candidate list for the hull star: coordinates relative to v (FP32), angular key
+// and slot per candidate, the candidates' order by angle (list indices), and the hull stack
+// (list indices); entry k of thread t at k * stride + t.
 struct HullList {
     float2 *xy;
     float *key;
     int *s;
+    unsigned char *ord;
     unsigned char *stk;
     int stride;
 };
 
-// Pseudo-angle of (x, y) in [0, 4): monotone in the polar angle (0 along +x, 1 along +y, ...).
+// Pseudo-angle of (x, y) in [0, 4): monotone in the polar angle (0 along +x, 1 along +y, ...);
+// the quadrant is decided by the signs of x and y, so the ends of the range never mix.
 __device__ __forceinline__ float pseudo_angle(float x, float y)
 {
     const float p = __fdividef(y, fabsf(x) + fabsf(y));
@@ -98,10 +101,10 @@ constexpr float KEY_EPS = 4e-6f;
 // and b; and the orientation of three images is the sign of the lifted incircle determinant of
 // (v, a, b, c) -- the predicate of the gift-wrapping search, with the same tie-break.  So the
 // hull's vertices in counter-clockwise order are v's star.  Steps: gather the candidates (the
-// nearest one, u0, is always a Delaunay neighbour), sort them by angle about v starting at u0,
-// one Graham scan, then certify every triangle (v, w_j, w_j+1) exactly as the gift-wrapping
-// search does (the circumcircle inside the searched region and within D of v).  Returns the
-// count, -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
+// nearest one, u0, is always a Delaunay neighbour), order them by angle about v, one Graham
+// scan starting at u0, then certify every triangle (v, w_j, w_j+1) as the gift-wrapping search
+// does (the circumcircle inside the searched region and within D of v).  Returns the count,
+// -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
 template <int KLC, typename Out>
 __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const Region &g, float D,
                                          const HullList &L, Out &&out)
@@ -121,6 +124,7 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
         dup |= (d.x | d.y) == 0;
         if (cnt == KLC) { over = true; return; }
         L.xy[cnt * S] = make_float2(fx, fy);
+        L.key[cnt * S] = pseudo_angle(fx, fy);
         L.s[cnt * S] = s;
         if (l <= lb * 1.000001f) {             // near the nearest so far: decide exactly
             const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
@@ -130,61 +134,38 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     });
     if (dup) return -PFEM_ERR_DEGENERATE;
     if (over || u0 < 0) return -1;
-    auto exact_of = [&](int slot) { return rel(__ldg(B.q + slot), pv); };
-    // angular keys relative to u0's direction (u0 first); candidates on u0's ray lie farther
-    // than u0 and cannot be neighbours: they are dropped (key +inf, sorted last)
-    const float2 U = L.xy[u0 * S];
-    const float ku = pseudo_angle(U.x, U.y);
-    const int2 du = exact_of(s0);
-    int live = 0;
-    for (int k = 0; k < cnt; ++k) {
-        float key = -1.f;
-        if (k != u0) {
-            const float2 c = L.xy[k * S];
-            key = pseudo_angle(c.x, c.y) - ku;
-            if (key < 0.f) key += 4.f;
-            if (key < KEY_EPS || key > 4.f - KEY_EPS) {          // near u0's ray: exactly
-                const int2 dc = exact_of(L.s[k * S]);
-                const long long cr = cross(du, dc);
-                if (cr > 0) key = key < 2.f ? key : 0.f;          // just counter-clockwise
-                else if (cr < 0) key = key > 2.f ? key : 4.f;     // just clockwise: last
-                else key = 3.4e38f;                               // on u0's ray
-            }
-        }
-        live += key < 1e30f;
-        L.key[k * S] = key;
-    }
-    // Should entry (kj, sj) come after (kc, sc)?  Near-equal keys are ordered by the exact cross
-    // product; on one ray the farther particle comes first (its image lies inside the hull and
-    // the scan removes it).
-    auto after = [&](float kj, int sj, float kc, int sc) -> bool {
-        if (kj - kc > KEY_EPS) return true;
-        if (kc - kj > KEY_EPS) return false;
-        if (kj > 1e30f || kc > 1e30f) return kj > kc;
-        const int2 dj = exact_of(sj), dc = exact_of(sc);
-        const long long cr = cross(dj, dc);
+    auto exact_of = [&](int k) { return rel(__ldg(B.q + L.s[k * S]), pv); };
+    // Order by angle (insertion sort of indices).  Should candidate a come after b?  Near-equal
+    // keys are ordered by the exact cross product, and on one ray the farther particle comes
+    // first: its image lies inside the hull and the scan removes it; on u0's ray this puts
+    // the farther particles just before u0, i.e. at the end of the scan that starts at u0.
+    auto after = [&](int a, float ka, int b, float kb) -> bool {
+        if (ka - kb > KEY_EPS) return true;
+        if (kb - ka > KEY_EPS) return false;
+        const int2 da = exact_of(a), db = exact_of(b);
+        const long long cr = cross(da, db);
         if (cr != 0) return cr < 0;
-        return (long long)dj.x * dj.x + (long long)dj.y * dj.y <
-               (long long)dc.x * dc.x + (long long)dc.y * dc.y;
+        return (long long)da.x * da.x + (long long)da.y * da.y <
+               (long long)db.x * db.x + (long long)db.y * db.y;
     };
+    L.ord[0] = 0;
     for (int i = 1; i < cnt; ++i) {
-        const float2 c = L.xy[i * S];
-        const float kc = L.key[i * S];
-        const int sc = L.s[i * S];
+        const float ki = L.key[i * S];
         int j = i - 1;
         for (; j >= 0; --j) {
-            const float kj = L.key[j * S];
-            const int sj = L.s[j * S];
-            if (!after(kj, sj, kc, sc)) break;
-            L.xy[(j + 1) * S] = L.xy[j * S];
-            L.key[(j + 1) * S] = kj;
-            L.s[(j + 1) * S] = sj;
+            const int oj = L.ord[j * S];
+            if (!after(oj, L.key[oj * S], i, ki)) break;
+            L.ord[(j + 1) * S] = (unsigned char)oj;
         }
-        L.xy[(j + 1) * S] = c;
-        L.key[(j + 1) * S] = kc;
-        L.s[(j + 1) * S] = sc;
+        L.ord[(j + 1) * S] = (unsigned char)i;
     }
-    // Graham scan from u0 (now entry 0) over the live entries
+    int p0 = 0;
+    for (int i = 0; i < cnt; ++i)
+        if (L.ord[i * S] == u0) p0 = i;
+    // Graham scan, cyclically from u0.  left(a, b, c): is the image of c to the left of the
+    // images of a -> b, i.e. c outside the circle through v, a, b?  FP32 filter on
+    // det = la (b x c) - lb (a x c) + lc (a x b), whose terms are bounded by
+    // la lb + lc (la + lb) (|p x q| <= (lp + lq) / 2); the exact predicate when undecided.
     auto left = [&](int a, int b, int c) -> bool {
         const float2 A = L.xy[a * S], Bp = L.xy[b * S], Cp = L.xy[c * S];
         const float la = fmaf(A.x, A.x, A.y * A.y), lbb = fmaf(Bp.x, Bp.x, Bp.y * Bp.y),
@@ -192,40 +173,39 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
         const float bc = fmaf(Bp.x, Cp.y, -Bp.y * Cp.x), ac = fmaf(A.x, Cp.y, -A.y * Cp.x),
                     ab = fmaf(A.x, Bp.y, -A.y * Bp.x);
         const float det = fmaf(la, bc, fmaf(-lbb, ac, lc * ab));
-        const float ra = sqrtf(la), rb = sqrtf(lbb), rc = sqrtf(lc);
-        const float mag = ra * rb * rc * (ra + rb + rc);
-        const float bnd = 1.9073486328125e-06f * mag;
+        const float bnd = 1.9073486328125e-06f * fmaf(la, lbb, lc * (la + lbb));
         if (det > bnd) return true;
         if (det < -bnd) return false;
-        const int sa = L.s[a * S], sb = L.s[b * S], sc = L.s[c * S];
-        const uint2 qa = __ldg(B.q + sa), qb = __ldg(B.q + sb), qc = __ldg(B.q + sc);
+        const uint2 qa = __ldg(B.q + L.s[a * S]), qb = __ldg(B.q + L.s[b * S]),
+                    qc = __ldg(B.q + L.s[c * S]);
         return incircle_exact(rel(qa, pv), rel(qb, pv), rel(qc, pv), pv, qa, qb, qc) < 0;
     };
-    int sp = 0;
-    L.stk[0] = 0;
-    sp = 1;
-    for (int i = 1; i < live; ++i) {
-        while (sp >= 2 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], i)) --sp;
-        L.stk[sp * S] = (unsigned char)i;
+    L.stk[0] = (unsigned char)u0;
+    int sp = 1;
+    for (int i = 1, p = p0 + 1; i < cnt; ++i, ++p) {
+        const int c = L.ord[(p == cnt ? (p = 0) : p) * S];
+        while (sp >= 2 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], c)) --sp;
+        L.stk[sp * S] = (unsigned char)c;
         ++sp;
     }
-    while (sp >= 3 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], 0)) --sp;
+    while (sp >= 3 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], u0)) --sp;
     if (sp < 3) return -1;
     // certify every triangle (v, w_j, w_j+1): counter-clockwise, circumcircle inside the region
-    // and within D of v (then no particle outside the list can lie inside it)
-    const float clx = g.cl_lo_x, chx = g.cl_hi_x, cly = g.cl_lo_y, chy = g.cl_hi_y;
+    // and within D of v (then no particle outside the list can lie inside it).  The circle
+    // through v, a, b has centre -(P, Q) / 2K and passes through v; its radius r must satisfy
+    // r + err <= every clearance measured from the centre and <= D / 2.
     for (int j = 0; j < sp; ++j) {
         const float2 a = L.xy[L.stk[j * S] * S];
         const float2 b = L.xy[L.stk[(j + 1 == sp ? 0 : j + 1) * S] * S];
         const FCirc cb = make_fcirc(a.x, a.y, b.x, b.y);
         if (!(cb.K > 1e-3f * cb.Ka)) return -1;
-        const float inv2k = 0.5f / cb.K;
-        const float ccx = -cb.P * inv2k, ccy = -cb.Q * inv2k;
-        const float r = sqrtf(fmaf(ccx, ccx, ccy * ccy));
-        const float err = 1e-4f * (cb.Pa + cb.Qa + (fabsf(cb.P) + fabsf(cb.Q)) * cb.Ka / cb.K) / cb.K + 64.f;
-        const float ext = r + err;
-        if (ccx - ext < -clx || ccx + ext > chx || ccy - ext < -cly || ccy + ext > chy) return -1;
-        if (2.f * ext > D * 0.9999f) return -1;
+        const float ik = __frcp_rn(cb.K);
+        const float ccx = -0.5f * cb.P * ik, ccy = -0.5f * cb.Q * ik;
+        const float err = (1e-4f * (cb.Pa + cb.Qa + (fabsf(cb.P) + fabsf(cb.Q)) * cb.Ka * ik)) * ik + 64.f;
+        const float room = fminf(fminf(fminf(g.cl_hi_x - ccx, g.cl_lo_x + ccx),
+                                       fminf(g.cl_hi_y - ccy, g.cl_lo_y + ccy)),
+                                 0.49995f * D) - err;
+        if (!(room > 0.f) || fmaf(ccx, ccx, ccy * ccy) > room * room * 0.9999f) return -1;
     }
     if (sp > B.kcap) return -PFEM_ERR_CAPACITY;
     for (int j = 0; j < sp; ++j) out(j, L.s[L.stk[j * S] * S]);
