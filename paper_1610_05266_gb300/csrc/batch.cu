@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(BSTAR) k_star_list_batch(const BPlanDev *pl, P
                                                            StarTab t)
 {
     __shared__ float2 sxy[STAR_KL * BSTAR];
-    __shared__ float skey[STAR_KL * BSTAR];
+    __shared__ unsigned skey[STAR_KL * BSTAR];
     __shared__ int ss[STAR_KL * BSTAR];
     __shared__ unsigned char sord[STAR_KL * BSTAR];
     __shared__ unsigned char sstk[STAR_KL * BSTAR];

@@ -120,6 +120,29 @@ __device__ __forceinline__ void for_region(const Bins &B, const Region &g, F &&f
     }
 }
 
+// The region's slots as contiguous runs f(first, end) (one per row, two where a row wraps).
+template <typename F>
+__device__ __forceinline__ void for_region_runs(const Bins &B, const Region &g, F &&f)
+{
+    const int nb = B.nb;
+    for (int dy = -g.R; dy <= g.R; ++dy) {
+        int by = g.by + dy;
+        by += by < 0 ? nb : 0;
+        by -= by >= nb ? nb : 0;
+        const int *row = B.start + (long long)by * nb;
+        const int x0 = g.bx - g.R, x1 = g.bx + g.R;       // inclusive
+        if (x0 >= 0 && x1 < nb) {
+            f(__ldg(row + x0), __ldg(row + x1 + 1));
+        } else if (x0 < 0) {
+            f(__ldg(row + x0 + nb), __ldg(row + nb));
+            f(__ldg(row), __ldg(row + x1 + 1));
+        } else {
+            f(__ldg(row + x0), __ldg(row + nb));
+            f(__ldg(row), __ldg(row + x1 - nb + 1));
+        }
+    }
+}
+
 // Circle through the origin v and points a, b (v, a, b counter-clockwise), as the lifted
 // determinant det3(c) = K |c|^2 + P cx + Q cy: c is strictly inside iff det3(c) < 0.
 // P, Q are rounded to FP32; Pa, Qa bound the magnitudes of the terms they were formed from.

@@ -10,7 +10,7 @@ namespace pfem {
 __global__ void __launch_bounds__(STAR_TPB) k_star_list(Bins B, int R0, StarTab t, DevStatus *st)
 {
     __shared__ float2 sxy[STAR_KL * STAR_TPB];
-    __shared__ float skey[STAR_KL * STAR_TPB];
+    __shared__ unsigned skey[STAR_KL * STAR_TPB];
     __shared__ int ss[STAR_KL * STAR_TPB];
     __shared__ unsigned char sord[STAR_KL * STAR_TPB];
     __shared__ unsigned char sstk[STAR_KL * STAR_TPB];

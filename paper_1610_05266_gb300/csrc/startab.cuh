@@ -62,21 +62,18 @@ static __device__ __noinline__ int locate_tab(const Bins &B, const StarTab &t, u
 }
 
 // Threads per block and candidate-list capacity of the list kernels.  The lists live in shared
-// memory, one column per thread (18 candidates x 17 bytes x 128 threads = 39 KB per block).
-// Jittered lattices have at most 17 particles within the 2-spacing cutoff; longer lists go to the
-// retry kernel.
+// memory, one column per thread (16 candidates x 18 bytes x 128 threads = 36 KB per block).
+// Jittered lattices at jitter 0.25 have at most 16 particles within the 2-spacing cutoff (rarely
+// 17 at jitter 0.3); longer lists go to the retry kernel.
 constexpr int STAR_TPB = 128;
-#ifndef PFEM_STAR_KL
-#define PFEM_STAR_KL 18
-#endif
-constexpr int STAR_KL = PFEM_STAR_KL;
+constexpr int STAR_KL = 16;
 
-// A thread's candidate list for the hull star: coordinates relative to v (FP32), angular key
-// and slot per candidate, the candidates' order by angle (list indices), and the hull stack
-// (list indices); entry k of thread t at k * stride + t.
+// A thread's candidate list for the hull star: coordinates relative to v (FP32), the packed
+// angular key, the slot, the order by angle and the hull stack; entry k of thread t at
+// k * stride + t.
 struct HullList {
     float2 *xy;
-    float *key;
+    unsigned *pk;
     int *s;
     unsigned char *ord;
     unsigned char *stk;
@@ -91,11 +88,37 @@ __device__ __forceinline__ float pseudo_angle(float x, float y)
     return x >= 0.f ? (y >= 0.f ? p : 4.f + p) : 2.f - p;
 }
 
-// Keys closer than this may be out of order after FP32 rounding (their error is below 1e-6):
-// such pairs are ordered exactly.
-constexpr float KEY_EPS = 4e-6f;
+// The key of candidate k, packed for sorting: the pseudo-angle in 27-bit fixed point (units of
+// 2^-25) above the 5-bit list index.  The pseudo-angle's FP32 error is below 1e-6, so keys that
+// differ by more than KEY_NEAR units are in the right order; closer ones are ordered exactly.
+constexpr unsigned KEY_NEAR = 134;   // 4e-6 * 2^25
+__device__ __forceinline__ unsigned pack_key(float x, float y, int k)
+{
+    const float a = fminf(pseudo_angle(x, y), 3.9999998f);
+    return ((unsigned)(a * 33554432.0f) << 5) | (unsigned)k;
+}
 
-// The Delaunay star of v from the candidates within distance D (capacity KLC), by the convex
+// Sort 16 packed keys (bitonic network, unrolled: the array stays in registers).
+__device__ __forceinline__ void sort16(unsigned (&w)[16])
+{
+#pragma unroll
+    for (int size = 2; size <= 16; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const unsigned a = w[i], b = w[j];
+                    const unsigned lo = min(a, b), hi = max(a, b);
+                    const bool up = (i & size) == 0;
+                    w[i] = up ? lo : hi;
+                    w[j] = up ? hi : lo;
+                }
+            }
+}
+
+// The Delaunay star of v from the candidates within distance D (at most 16), by the convex
 // hull of the candidates inverted about v.  Inversion c -> c/|c|^2 maps the circles through v
 // to lines, so an empty circle through v, a, b becomes a hull edge between the images of a
 // and b; and the orientation of three images is the sign of the lifted incircle determinant of
@@ -105,90 +128,146 @@ constexpr float KEY_EPS = 4e-6f;
 // scan starting at u0, then certify every triangle (v, w_j, w_j+1) as the gift-wrapping search
 // does (the circumcircle inside the searched region and within D of v).  Returns the count,
 // -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
-template <int KLC, typename Out>
+template <typename Out>
 __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const Region &g, float D,
                                          const HullList &L, Out &&out)
 {
+    constexpr int KLC = 16;
     const int S = L.stride;
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
     float lb = 3.4e38f;
     bool dup = false, over = false;
     const float D2 = D * D;
-    for_region(B, g, [&](int s) {
+    auto take = [&](int s, uint2 qs) {
         if (s == v) return;
-        const int2 d = rel(__ldg(B.q + s), pv);
+        const int2 d = rel(qs, pv);
         const float fx = (float)d.x, fy = (float)d.y;
         const float l = fmaf(fx, fx, fy * fy);
         if (l > D2) return;
         dup |= (d.x | d.y) == 0;
         if (cnt == KLC) { over = true; return; }
         L.xy[cnt * S] = make_float2(fx, fy);
-        L.key[cnt * S] = pseudo_angle(fx, fy);
+        L.pk[cnt * S] = pack_key(fx, fy, cnt);
         L.s[cnt * S] = s;
         if (l <= lb * 1.000001f) {             // near the nearest so far: decide exactly
             const long long d2 = (long long)d.x * d.x + (long long)d.y * d.y;
             if (d2 < d2b || (d2 == d2b && s < s0)) { d2b = d2; u0 = cnt; s0 = s; lb = l; }
         }
         ++cnt;
+    };
+    // the region's slot runs, four loads in flight at a time
+    for_region_runs(B, g, [&](int a, int e) {
+        int s = a;
+        for (; s + 4 <= e; s += 4) {
+            const uint2 q0 = __ldg(B.q + s), q1 = __ldg(B.q + s + 1), q2 = __ldg(B.q + s + 2),
+                        q3 = __ldg(B.q + s + 3);
+            take(s, q0);
+            take(s + 1, q1);
+            take(s + 2, q2);
+            take(s + 3, q3);
+        }
+        for (; s < e; ++s) take(s, __ldg(B.q + s));
     });
     if (dup) return -PFEM_ERR_DEGENERATE;
     if (over || u0 < 0) return -1;
     auto exact_of = [&](int k) { return rel(__ldg(B.q + L.s[k * S]), pv); };
-    // Order by angle (insertion sort of indices).  Should candidate a come after b?  Near-equal
-    // keys are ordered by the exact cross product, and on one ray the farther particle comes
-    // first: its image lies inside the hull and the scan removes it; on u0's ray this puts
-    // the farther particles just before u0, i.e. at the end of the scan that starts at u0.
-    auto after = [&](int a, float ka, int b, float kb) -> bool {
-        if (ka - kb > KEY_EPS) return true;
-        if (kb - ka > KEY_EPS) return false;
-        const int2 da = exact_of(a), db = exact_of(b);
-        const long long cr = cross(da, db);
-        if (cr != 0) return cr < 0;
-        return (long long)da.x * da.x + (long long)da.y * da.y <
-               (long long)db.x * db.x + (long long)db.y * db.y;
-    };
-    L.ord[0] = 0;
-    for (int i = 1; i < cnt; ++i) {
-        const float ki = L.key[i * S];
-        int j = i - 1;
-        for (; j >= 0; --j) {
-            const int oj = L.ord[j * S];
-            if (!after(oj, L.key[oj * S], i, ki)) break;
-            L.ord[(j + 1) * S] = (unsigned char)oj;
-        }
-        L.ord[(j + 1) * S] = (unsigned char)i;
-    }
+    // Order by angle: the packed keys through the network, then an exact pass over keys closer
+    // than KEY_NEAR (near-equal angles by the exact cross product; on one ray the farther
+    // particle first: its image lies inside the hull and the scan removes it, and on u0's ray
+    // this puts the farther particles just before u0, i.e. at the end of the scan from u0).
+    unsigned w[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = k < cnt ? L.pk[k * S] : 0xffffffffu;
+    sort16(w);
+    bool near = false;
     int p0 = 0;
-    for (int i = 0; i < cnt; ++i)
-        if (L.ord[i * S] == u0) p0 = i;
-    // Graham scan, cyclically from u0.  left(a, b, c): is the image of c to the left of the
-    // images of a -> b, i.e. c outside the circle through v, a, b?  FP32 filter on
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < cnt) L.ord[k * S] = (unsigned char)(w[k] & 31u);
+        if (k + 1 < cnt && (w[k + 1] >> 5) - (w[k] >> 5) < KEY_NEAR) near = true;
+        if (k < cnt && (int)(w[k] & 31u) == u0) p0 = k;
+    }
+    if (near) {
+        auto after = [&](int a, int b) -> bool {   // should candidate a come after b?
+            const unsigned ka = L.pk[a * S] >> 5, kb = L.pk[b * S] >> 5;
+            if (ka > kb + KEY_NEAR) return true;
+            if (kb > ka + KEY_NEAR) return false;
+            const int2 da = exact_of(a), db = exact_of(b);
+            const long long cr = cross(da, db);
+            if (cr != 0) return cr < 0;
+            return (long long)da.x * da.x + (long long)da.y * da.y <
+                   (long long)db.x * db.x + (long long)db.y * db.y;
+        };
+        for (int i = 1; i < cnt; ++i) {
+            const int oi = L.ord[i * S];
+            int j = i - 1;
+            for (; j >= 0; --j) {
+                const int oj = L.ord[j * S];
+                if (!after(oj, oi)) break;
+                L.ord[(j + 1) * S] = (unsigned char)oj;
+            }
+            L.ord[(j + 1) * S] = (unsigned char)oi;
+        }
+        for (int k = 0; k < cnt; ++k)
+            if (L.ord[k * S] == u0) p0 = k;
+    }
+    // Graham scan, cyclically from u0.  Is the image of c to the left of the images of a -> b,
+    // i.e. c outside the circle through v, a, b?  FP32 filter on
     // det = la (b x c) - lb (a x c) + lc (a x b), whose terms are bounded by
     // la lb + lc (la + lb) (|p x q| <= (lp + lq) / 2); the exact predicate when undecided.
-    auto left = [&](int a, int b, int c) -> bool {
-        const float2 A = L.xy[a * S], Bp = L.xy[b * S], Cp = L.xy[c * S];
-        const float la = fmaf(A.x, A.x, A.y * A.y), lbb = fmaf(Bp.x, Bp.x, Bp.y * Bp.y),
-                    lc = fmaf(Cp.x, Cp.x, Cp.y * Cp.y);
-        const float bc = fmaf(Bp.x, Cp.y, -Bp.y * Cp.x), ac = fmaf(A.x, Cp.y, -A.y * Cp.x),
-                    ab = fmaf(A.x, Bp.y, -A.y * Bp.x);
-        const float det = fmaf(la, bc, fmaf(-lbb, ac, lc * ab));
-        const float bnd = 1.9073486328125e-06f * fmaf(la, lbb, lc * (la + lbb));
+    // The two top entries of the stack are kept in registers.
+    auto xyl = [&](int k, float &x, float &y, float &l) {
+        const float2 t = L.xy[k * S];
+        x = t.x;
+        y = t.y;
+        l = fmaf(x, x, y * y);
+    };
+    int ia = -1, ib = u0;
+    float ax = 0.f, ay = 0.f, la = 0.f, bx, by, lbv;
+    xyl(u0, bx, by, lbv);
+    float ab = 0.f;
+    L.stk[0] = (unsigned char)u0;
+    int sp = 1;
+    auto left = [&](int c, float cx, float cy, float lc) -> bool {
+        const float bc = fmaf(bx, cy, -by * cx), ac = fmaf(ax, cy, -ay * cx);
+        const float det = fmaf(la, bc, fmaf(-lbv, ac, lc * ab));
+        const float bnd = 1.9073486328125e-06f * fmaf(la, lbv, lc * (la + lbv));
         if (det > bnd) return true;
         if (det < -bnd) return false;
-        const uint2 qa = __ldg(B.q + L.s[a * S]), qb = __ldg(B.q + L.s[b * S]),
+        const uint2 qa = __ldg(B.q + L.s[ia * S]), qb = __ldg(B.q + L.s[ib * S]),
                     qc = __ldg(B.q + L.s[c * S]);
         return incircle_exact(rel(qa, pv), rel(qb, pv), rel(qc, pv), pv, qa, qb, qc) < 0;
     };
-    L.stk[0] = (unsigned char)u0;
-    int sp = 1;
+    auto pop = [&]() {
+        --sp;
+        ib = ia;
+        bx = ax;
+        by = ay;
+        lbv = la;
+        if (sp >= 2) {
+            ia = L.stk[(sp - 2) * S];
+            xyl(ia, ax, ay, la);
+            ab = fmaf(ax, by, -ay * bx);
+        }
+    };
     for (int i = 1, p = p0 + 1; i < cnt; ++i, ++p) {
-        const int c = L.ord[(p == cnt ? (p = 0) : p) * S];
-        while (sp >= 2 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], c)) --sp;
+        if (p == cnt) p = 0;
+        const int c = L.ord[p * S];
+        float cx, cy, lc;
+        xyl(c, cx, cy, lc);
+        while (sp >= 2 && !left(c, cx, cy, lc)) pop();
         L.stk[sp * S] = (unsigned char)c;
         ++sp;
+        ia = ib; ax = bx; ay = by; la = lbv;
+        ib = c; bx = cx; by = cy; lbv = lc;
+        ab = fmaf(ax, by, -ay * bx);
     }
-    while (sp >= 3 && !left(L.stk[(sp - 2) * S], L.stk[(sp - 1) * S], u0)) --sp;
+    {
+        float cx, cy, lc;
+        xyl(u0, cx, cy, lc);
+        while (sp >= 3 && !left(u0, cx, cy, lc)) pop();
+    }
     if (sp < 3) return -1;
     // certify every triangle (v, w_j, w_j+1): counter-clockwise, circumcircle inside the region
     // and within D of v (then no particle outside the list can lie inside it).  The circle
@@ -220,7 +299,7 @@ __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const Star
     int *out = t.nbr + v * KMAX;
     int c = -1;
     if (B.dmax > 0.f)
-        c = star_hull<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
+        c = star_hull(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
                                [&](int k, int s) { out[k] = s; });
     if (c == -1) {
         t.cnt[v] = -1;
