@@ -177,7 +177,9 @@ pfem_status pfem_build_cells(pfem_ctx *ctx, int32_t nb, int64_t N, const void *p
  * bytes), held on every GPU that loads it until the process exits; this call allocates nothing.
  * Limits: N <= 4,194,304 particles and nb*nb <= 1,048,576 bins, else PFEM_ERR_CAPACITY
  * (nothing launched).  The first call on a device looks up the scratch's device address (with
- * that device current) and caches it: make that first call before any stream capture.  All
+ * that device current) and caches it: make that first call before any stream capture.  The
+ * cached address belongs to the device's primary context: after the host application destroys
+ * that context (cudaDeviceReset), this entry point must not be called again in the process.  All
  * calls share the one scratch array and it keeps the last call's contents (the bin counters
  * are cleared at the start of every call): calls that overlap on the GPU -- on different
  * streams without ordering, or from different host threads -- race and must not be issued. */

@@ -5,9 +5,9 @@
 //
 // Steps: (1) per particle: fixed point, bin, and an arrival rank inside the bin (atomic
 // counter; order not yet deterministic); (2) exclusive scan of the bin counts; (3) scatter to
-// slot start + rank; (4) per bin: insertion-sort its slots by original index (bins hold a few
-// particles), which makes the order stable and bit-reproducible; (5) per slot: gather sorted
-// positions and fixed-point coordinates (coalesced writes).
+// slot start + rank; (4) per particle: its rank by original index within its bin, which makes
+// the order stable and bit-reproducible; (5) per slot: gather sorted positions and fixed-point
+// coordinates (coalesced writes).
 #include "internal.h"
 
 namespace pfem {
@@ -34,31 +34,37 @@ __global__ void k_scatter(long long N, const int *__restrict__ key, const int *_
         perm[__ldg(cell_start + key[m]) + rank[m]] = (int)m;
 }
 
-__global__ void k_sort_bins(long long nbins, const int *__restrict__ cell_start, int *perm)
+// Order each bin's slots by original index: the slot of particle m in bin b is
+// cell_start[b] + #{particles of b with a smaller index}.  One thread per particle counts over
+// its bin (the scatter left the bin's particles in arrival order), so a crowded bin costs
+// parallel work, not a serial sort.
+__global__ void k_rank_bins(long long N, const int *__restrict__ key,
+                            const int *__restrict__ cell_start, const int *__restrict__ perm,
+                            int *__restrict__ sorted)
 {
-    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbins;
-         b += (long long)gridDim.x * blockDim.x) {
-        const int s0 = cell_start[b], s1 = cell_start[b + 1];
-        for (int i = s0 + 1; i < s1; ++i) {
-            const int v = perm[i];
-            int j = i - 1;
-            while (j >= s0 && perm[j] > v) {
-                perm[j + 1] = perm[j];
-                --j;
-            }
-            perm[j + 1] = v;
-        }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int m = perm[i];
+        const int b = __ldg(key + m);
+        const int s0 = __ldg(cell_start + b), s1 = __ldg(cell_start + b + 1);
+        int r = 0;
+        for (int j = s0; j < s1; ++j) r += perm[j] < m;
+        sorted[s0 + r] = m;
     }
 }
 
+// Final order (from k_rank_bins) into perm, and the positions and fixed-point coordinates in
+// slot order (coalesced writes).
 template <typename P>
-__global__ void k_gather(long long N, const P *__restrict__ pos, const int *__restrict__ perm,
-                         P *__restrict__ pos_sorted, uint2 *__restrict__ q_sorted)
+__global__ void k_gather(long long N, const P *__restrict__ pos, const int *__restrict__ sorted,
+                         int *__restrict__ perm, P *__restrict__ pos_sorted,
+                         uint2 *__restrict__ q_sorted)
 {
     using V2 = typename Vec2<P>::type;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
-        const int m = __ldg(perm + s);
+        const int m = __ldg(sorted + s);
+        perm[s] = m;
         const V2 v = __ldg(reinterpret_cast<const V2 *>(pos) + m);
         reinterpret_cast<V2 *>(pos_sorted)[s] = v;
         q_sorted[s] = make_uint2(fx_of(v.x), fx_of(v.y));
@@ -156,20 +162,22 @@ static unsigned grid_for(long long work, int threads)
 // Scatter to slot start + rank, order each bin by original index, gather sorted positions.
 template <typename P>
 static cudaError_t sort_gather_t(long long nbins, long long N, const P *pos, const int *key,
-                                 const int *rank, const int *cell_start, int *perm, P *pos_sorted,
+                                 int *rank, const int *cell_start, int *perm, P *pos_sorted,
                                  uint2 *q_sorted, cudaStream_t s)
 {
     if (N > 0) {
+        // the arrival ranks are dead after the scatter: their array takes the final order
+        int *sorted = rank;
         k_scatter<<<grid_for(N, 256), 256, 0, s>>>(N, key, rank, cell_start, perm);
-        k_sort_bins<<<grid_for(nbins, 128), 128, 0, s>>>(nbins, cell_start, perm);
-        k_gather<P><<<grid_for(N, 256), 256, 0, s>>>(N, pos, perm, pos_sorted, q_sorted);
+        k_rank_bins<<<grid_for(N, 256), 256, 0, s>>>(N, key, cell_start, perm, sorted);
+        k_gather<P><<<grid_for(N, 256), 256, 0, s>>>(N, pos, sorted, perm, pos_sorted, q_sorted);
         count_launch(3);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort_gather(long long nbins, long long N, const void *pos, pfem_dtype pos_t,
-                               const int *key, const int *rank, const int *cell_start, int *perm,
+                               const int *key, int *rank, const int *cell_start, int *perm,
                                void *pos_sorted, uint32_t *q_sorted, cudaStream_t s)
 {
     if (pos_t == PFEM_F64)

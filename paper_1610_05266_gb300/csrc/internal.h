@@ -24,7 +24,7 @@ struct WsLayout {
 WsLayout ws_layout(int n, int nb, long long N, int C);
 WsLayout ws_layout_bins(long long nbins, long long N);
 cudaError_t launch_sort_gather(long long nbins, long long N, const void *pos, pfem_dtype pos_t,
-                               const int *key, const int *rank, const int *cell_start, int *perm,
+                               const int *key, int *rank, const int *cell_start, int *perm,
                                void *pos_sorted, uint32_t *q_sorted, cudaStream_t s);
 size_t batch_plan_bytes(int P);
 int batch_plan_build(int P, const pfem_batch_problem *probs, void *plan_dev, long long *N_total,

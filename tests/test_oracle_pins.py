@@ -385,6 +385,38 @@ def test_p2m_position_gradient_vs_central_differences(small, shape):
     assert checked >= 16
 
 
+@pytest.mark.parametrize("shape", [0, 1])
+def test_node_weight_derivatives_vs_central_differences(small, shape):
+    """The complex-step derivative of one node's weights with respect to one particle
+    coordinate equals the central difference of the weights themselves (step 1e-6, FP64) for
+    every particle of the node's weight set, when the perturbation leaves the topology alone.
+    A wrong sign or a dropped chain-rule term in the complex-step path would fail this."""
+    n, pos, _, _ = small
+    cells = O.build_cells(n, pos)
+    rng = np.random.default_rng(17)
+    checked = 0
+    for node in rng.choice(n * n, 10, replace=False):
+        J, I = divmod(int(node), n)
+        idx, w, _, _ = O.node_weights(cells, I, J, shape)
+        for m in rng.choice(idx, 2, replace=False):
+            for dim in (0, 1):
+                didx, dw = O.node_weight_derivs(cells, I, J, int(m), dim, shape)
+                assert np.array_equal(didx, idx)
+                step = 1e-6
+                pp, pm = pos.copy(), pos.copy()
+                pp[m, dim] += step
+                pm[m, dim] -= step
+                ip, wp, _, _ = O.node_weights(O.build_cells(n, pp), I, J, shape)
+                im, wm, _, _ = O.node_weights(O.build_cells(n, pm), I, J, shape)
+                if sorted(ip) != sorted(idx) or sorted(im) != sorted(idx):
+                    continue
+                fp = dict(zip(ip.tolist(), wp)); fm = dict(zip(im.tolist(), wm))
+                fd = np.array([(fp[k] - fm[k]) / (2 * step) for k in idx.tolist()])
+                assert np.abs(fd - dw).max() <= 1e-6 * max(1.0, np.abs(fd).max()), (I, J, m, dim)
+                checked += 1
+    assert checked >= 20
+
+
 def test_m2p_adjoint(small):
     """M2P: <M2P f, g> = <f, M2P^T g>, and the position gradient vs central differences."""
     n, pos, vals, _ = small
