@@ -939,10 +939,41 @@ static void coffset(const Geo *g, int32_t slot, double xq, double yq, int32_t ks
 }
 
 /* Node weights with complex positions, for the complex-step derivative.  Same construction
- * as node_weights, except that the per-edge minimum-norm A comes from the normal equations
- * (P P^T) y = b, A = P^T y, with a complex-symmetric Cholesky factorisation (analytic in
- * the positions); for a full-rank stencil this is the same A as the SVD route.  Topology
- * and the frame (centre, scale) are taken from the real parts. */
+ * as node_weights, with every step analytic in the positions: the edge frame (midpoint and
+ * length) is formed from the complex offsets too, and the per-edge A comes from the normal
+ * equations instead of the SVD route -- for a stencil of k >= 6 particles the minimum-norm
+ * solution A = P^T y with (P P^T) y = b, for k < 6 (P of full column rank k: five particles
+ * lie on one conic, so the six conditions cannot all hold) the least-squares solution
+ * A = (P^T P)^-1 P^T b; both equal the pseudo-inverse solution P^+ b of the SVD route.  The
+ * symmetric systems are factorised by a complex-symmetric Cholesky.  Topology is taken from
+ * the real parts. */
+static void csym_cholesky_solve(int m, cplx G[][6], cplx *rhs, cplx *x)
+{
+    cplx L[6][6], z[6];
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) L[r][c] = 0;
+    for (int c = 0; c < m; ++c) {
+        cplx acc = G[c][c];
+        for (int j = 0; j < c; ++j) acc -= L[c][j] * L[c][j];
+        L[c][c] = __builtin_csqrt(acc);
+        for (int r = c + 1; r < m; ++r) {
+            cplx a2 = G[r][c];
+            for (int j = 0; j < c; ++j) a2 -= L[r][j] * L[c][j];
+            L[r][c] = a2 / L[c][c];
+        }
+    }
+    for (int r = 0; r < m; ++r) {
+        cplx acc = rhs[r];
+        for (int j = 0; j < r; ++j) acc -= L[r][j] * z[j];
+        z[r] = acc / L[r][r];
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        cplx acc = z[r];
+        for (int j = r + 1; j < m; ++j) acc -= L[j][r] * x[j];
+        x[r] = acc / L[r][r];
+    }
+}
+
 static void node_weights_cplx(const Geo *g, const NodeQ *Q, int I, int J, int shape,
                               int32_t kslot, int dim, double h, CSet *out)
 {
@@ -963,9 +994,9 @@ static void node_weights_cplx(const Geo *g, const NodeQ *Q, int I, int J, int sh
         int f = (e + 1) % 3;
         int S[2 + 2 * OR_KSTAR];
         int k = edge_stencil(Q, e, S);
-        double mx = 0.5 * __real__(d[e][0] + d[f][0]), my = 0.5 * __real__(d[e][1] + d[f][1]);
-        double ex = __real__(d[e][0] - d[f][0]), ey = __real__(d[e][1] - d[f][1]);
-        double s = sqrt(ex * ex + ey * ey);
+        cplx mx = 0.5 * (d[e][0] + d[f][0]), my = 0.5 * (d[e][1] + d[f][1]);
+        cplx ex = d[e][0] - d[f][0], ey = d[e][1] - d[f][1];
+        cplx s = __builtin_csqrt(ex * ex + ey * ey);
         cplx p[OR_KSTEN][6];
         for (int i = 0; i < k; ++i) {
             cplx dx, dy;
@@ -973,41 +1004,35 @@ static void node_weights_cplx(const Geo *g, const NodeQ *Q, int I, int J, int sh
             cplx x = (dx - mx) / s, y = (dy - my) / s;
             p[i][0] = 1; p[i][1] = x; p[i][2] = y; p[i][3] = x * x; p[i][4] = x * y; p[i][5] = y * y;
         }
-        cplx tx = (d[e][0] - d[f][0]) / s, ty = (d[e][1] - d[f][1]) / s;
+        cplx tx = ex / s, ty = ey / s;
         cplx b[6] = {0, 0, 0, -0.5 * tx * tx, -0.5 * tx * ty, -0.5 * ty * ty};
-        cplx M[6][6], L[6][6], z[6], y[6];
-        for (int r = 0; r < 6; ++r)
-            for (int c = 0; c < 6; ++c) {
-                M[r][c] = 0;
-                L[r][c] = 0;
-                for (int i = 0; i < k; ++i) M[r][c] += p[i][r] * p[i][c];
+        cplx A[OR_KSTEN];
+        if (k >= 6) {
+            cplx M[6][6], y[6];
+            for (int r = 0; r < 6; ++r)
+                for (int c = 0; c < 6; ++c) {
+                    M[r][c] = 0;
+                    for (int i = 0; i < k; ++i) M[r][c] += p[i][r] * p[i][c];
+                }
+            csym_cholesky_solve(6, M, b, y);
+            for (int i = 0; i < k; ++i) {
+                A[i] = 0;
+                for (int r = 0; r < 6; ++r) A[i] += p[i][r] * y[r];
             }
-        for (int c = 0; c < 6; ++c) {
-            cplx acc = M[c][c];
-            for (int j = 0; j < c; ++j) acc -= L[c][j] * L[c][j];
-            L[c][c] = __builtin_csqrt(acc);
-            for (int r = c + 1; r < 6; ++r) {
-                cplx a2 = M[r][c];
-                for (int j = 0; j < c; ++j) a2 -= L[r][j] * L[c][j];
-                L[r][c] = a2 / L[c][c];
+        } else {
+            cplx Gm[6][6], rhs[6];
+            for (int i = 0; i < k; ++i) {
+                rhs[i] = 0;
+                for (int r = 0; r < 6; ++r) rhs[i] += p[i][r] * b[r];
+                for (int j = 0; j < k; ++j) {
+                    Gm[i][j] = 0;
+                    for (int r = 0; r < 6; ++r) Gm[i][j] += p[i][r] * p[j][r];
+                }
             }
-        }
-        for (int r = 0; r < 6; ++r) {
-            cplx acc = b[r];
-            for (int j = 0; j < r; ++j) acc -= L[r][j] * z[j];
-            z[r] = acc / L[r][r];
-        }
-        for (int r = 5; r >= 0; --r) {
-            cplx acc = z[r];
-            for (int j = r + 1; j < 6; ++j) acc -= L[j][r] * y[j];
-            y[r] = acc / L[r][r];
+            csym_cholesky_solve(k, Gm, rhs, A);
         }
         cplx cf = 2.0 * lam[e] * lam[f];
-        for (int i = 0; i < k; ++i) {
-            cplx A = 0;
-            for (int r = 0; r < 6; ++r) A += p[i][r] * y[r];
-            cset_add(out, Q->w.p[S[i]].slot, cf * A);
-        }
+        for (int i = 0; i < k; ++i) cset_add(out, Q->w.p[S[i]].slot, cf * A[i]);
     }
 }
 

@@ -417,6 +417,37 @@ def test_node_weight_derivatives_vs_central_differences(small, shape):
     assert checked >= 20
 
 
+def test_rank_deficient_node_derivatives_vs_central_differences():
+    """512^2 uniform random particles on the 257^2 mesh: node (68, 52) has an edge whose
+    stencil is five particles, so its system is inconsistent and the oracle's forward takes the
+    least-squares pseudo-inverse solution by SVD (App. A), which depends on the edge frame.  The
+    complex-step derivative (normal equations of the five-column system, frame differentiated)
+    matches central differences of the SVD forward (step 1e-7) for every particle of the node's
+    weight set in both coordinates."""
+    n, M = 257, 512
+    pos = G.uniform01(G.SEED_BASE + 62, 2 * M * M).reshape(M * M, 2)
+    cells = O.build_cells(n, pos)
+    I, J = 68, 52
+    idx, w, _, rank = O.node_weights(cells, I, J, 1)
+    assert rank == 5
+    checked = 0
+    for m in idx.tolist():
+        for dim in (0, 1):
+            didx, dw = O.node_weight_derivs(cells, I, J, m, dim, 1)
+            step = 1e-7
+            pp, pm = pos.copy(), pos.copy()
+            pp[m, dim] += step
+            pm[m, dim] -= step
+            ip, wp, _, rp = O.node_weights(O.build_cells(n, pp), I, J, 1)
+            im, wm, _, rm = O.node_weights(O.build_cells(n, pm), I, J, 1)
+            assert sorted(ip) == sorted(idx) and sorted(im) == sorted(idx) and rp == rm == 5
+            fp = dict(zip(ip.tolist(), wp)); fm = dict(zip(im.tolist(), wm))
+            fd = np.array([(fp[k] - fm[k]) / (2 * step) for k in idx.tolist()])
+            assert np.abs(fd - dw).max() <= 1e-5 * max(1.0, np.abs(fd).max()), (m, dim)
+            checked += 1
+    assert checked == 2 * len(idx)
+
+
 def test_m2p_adjoint(small):
     """M2P: <M2P f, g> = <f, M2P^T g>, and the position gradient vs central differences."""
     n, pos, vals, _ = small
