@@ -15,6 +15,8 @@
 // Determinism without atomics on values: phase 1 writes each node's entries (slot, w, dpos)
 // into [n*n, K] arrays; phase 2 builds a transposed index by a stable counting sort keyed by
 // particle slot (entries per particle ordered by entry id) and gathers per particle.
+#include <algorithm>
+
 #include "internal.h"
 #include "p2m.cuh"
 
@@ -33,7 +35,8 @@ constexpr int KBWD = 32;   // distinct particles per node kept by the recompute 
 
 // The adjoint of one node over its particle set (us[0..nu), stencil masks vm, tri[e] = us[vi[e]]):
 // uw the weights, ub = gbar . alpha per particle, udx/udy the position adjoints (all zero on
-// entry).  Returns 0 or -PFEM_ERR_DEGENERATE (a moment matrix that cannot be factored).
+// entry).  Returns 0, or -PFEM_DEFER when a moment matrix is below the forward's fast-solve
+// tolerance: the node goes to the adjoint's fix pass, as the forward sends it to its own.
 template <typename P, typename V, typename R, typename S, int SHAPE, bool POS>
 __device__ __forceinline__ int bwd_u_solve(const BwdArgs &b, const NodePos<P, R> &np, const R g[8],
                                            const int tri[3], const int *us, int nu,
@@ -93,7 +96,7 @@ __device__ __forceinline__ int bwd_u_solve(const BwdArgs &b, const NodePos<P, R>
 #pragma unroll
                 for (int r = 0; r < 6; ++r) u[r] = fma(bt, p[r], u[r]);
             }
-            if (!M.factor(SolveTol<S>::v)) { st = -PFEM_ERR_DEGENERATE; break; }
+            if (!M.factor(FastTol<S>::v)) { st = -PFEM_DEFER; break; }
             const S tx = ex * inv, ty = ey * inv;
             const S bb[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty,
                              S(-0.5) * ty * ty};
@@ -220,13 +223,14 @@ __device__ __forceinline__ void bwd_node(const BwdArgs &b, int I, int J)
                     for (int i = 0; i < ns[e]; ++i) m |= 1u << add(stars[e][i]);
                     vm[e] = m;
                 }
-            if (over) st = -PFEM_ERR_CAPACITY;
+            if (over) st = -PFEM_DEFER;
             if (st == 0)
                 st = bwd_u_solve<P, V, R, S, SHAPE, POS>(b, np, g, tri, us, nu, vm, vi, uw, ub,
                                                          udx, udy);
         }
         if (st != 0) {
-            record_error(a.status, -st, node);
+            st = defer_or_error(a, st, node);
+            if (st < 0) record_error(a.status, -st, node);
             nu = 0;
         }
     }
@@ -295,10 +299,11 @@ __global__ void __launch_bounds__(128, 4) k_bwd_solve(BwdArgs b, NodeRecs r)
             const int I = (int)(node % a.n), J = (int)(node / a.n);
             NodePos<P, R> np;
             np.init(I == nc ? 0 : I, J == nc ? 0 : J, nc);
-            const int st = bwd_u_solve<P, V, R, S, PFEM_SHAPE_QUADRATIC, POS>(
+            int st = bwd_u_solve<P, V, R, S, PFEM_SHAPE_QUADRATIC, POS>(
                 b, np, g, tri, us, nu, vm, vi, uw, ub, udx, udy);
             if (st != 0) {
-                record_error(a.status, -st, node);
+                st = defer_or_error(a, st, node);
+                if (st < 0) record_error(a.status, -st, node);
                 nu = 0;
             }
         }
@@ -310,6 +315,256 @@ __global__ void __launch_bounds__(128, 4) k_bwd_solve(BwdArgs b, NodeRecs r)
         if (POS) {
             od[2 * k] = v ? udx[k] : R(0);
             od[2 * k + 1] = v ? udy[k] : R(0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fix pass
+// The nodes the fast adjoint queued (an edge system below the forward's fast-solve tolerance,
+// more particles than the fast pass holds, or a search that ran out of its region), recomputed
+// in FP64 with the forward fix pass's geometry (widest search radius) and SVD solve.  For each
+// edge, with P the 6 x k monomial matrix (the stencil in the edge frame), A = P^+ b its
+// pseudo-inverse solution and Abar = c_e beta, the reverse-mode derivative of the pseudo-inverse
+// at constant rank (Golub & Pereyra 1973) gives
+//   Pbar = -u A^T + r (P^+ u)^T + z ((I - P^+ P) Abar)^T,   bbar = u,
+// with u = P^+T Abar, z = P^+T A and r = b - P A (zero unless the system is inconsistent, as
+// for a stencil of five particles).  A least-squares solution depends on the edge frame, so the
+// frame's dependence on the edge endpoints (midpoint m, length s) is differentiated too.
+
+// One edge.  pt: the k members' monomial rows (overwritten), x/y their frame coordinates,
+// beta their gbar . alpha, b, ce = 2 lambda_nu lambda_sg.  Out: A (coefficients), xb/yb the
+// adjoints of the members' frame coordinates, bb the adjoint of b, and Be = sum beta A.
+static __device__ __noinline__ void edge_adjoint_svd(int k, double (*pt)[6], const double *x,
+                                                     const double *y, const double *beta,
+                                                     const double b[6], double ce, double *A,
+                                                     double *xb, double *yb, double bb[6],
+                                                     double &Be)
+{
+    double V[6][6], sig2[6];
+    jacobi_svd(k, pt, V, sig2);
+    const double thr2 = svd_threshold2(k, sig2);
+    double vb[6], wA[6], wAA[6];
+    for (int j = 0; j < 6; ++j) {
+        double d = 0.0;
+        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
+        vb[j] = sig2[j] > thr2 ? d : 0.0;
+    }
+    Be = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double a = 0.0;
+        for (int j = 0; j < 6; ++j)
+            if (sig2[j] > thr2) a = fma(vb[j] / sig2[j], pt[i][j], a);
+        A[i] = a;
+        Be = fma(beta[i], a, Be);
+    }
+    for (int j = 0; j < 6; ++j) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = 0; i < k; ++i) {
+            s1 = fma(pt[i][j], ce * beta[i], s1);
+            s2 = fma(pt[i][j], A[i], s2);
+        }
+        wA[j] = sig2[j] > thr2 ? s1 / sig2[j] : 0.0;    // (w_j . Abar) / sigma_j^2
+        wAA[j] = sig2[j] > thr2 ? s2 / sig2[j] : 0.0;   // (w_j . A) / sigma_j^2
+    }
+    double u[6], z[6], r[6];
+    for (int q = 0; q < 6; ++q) {
+        double su = 0.0, sz = 0.0, sr = b[q];
+        for (int j = 0; j < 6; ++j) {
+            su = fma(V[q][j], wA[j], su);
+            sz = fma(V[q][j], wAA[j], sz);
+            sr = fma(-V[q][j], vb[j], sr);
+        }
+        u[q] = su;
+        z[q] = sz;
+        r[q] = sr;
+        bb[q] = su;
+    }
+    for (int i = 0; i < k; ++i) {
+        double pu = 0.0, pp = 0.0;
+        for (int j = 0; j < 6; ++j)
+            if (sig2[j] > thr2) {
+                pu = fma(pt[i][j], wA[j] / sig2[j], pu);
+                pp = fma(pt[i][j], wA[j], pp);
+            }
+        const double qi = ce * beta[i] - pp;              // ((I - P^+ P) Abar)_i
+        double pb[6];
+        for (int q = 0; q < 6; ++q) pb[q] = -u[q] * A[i] + r[q] * pu + z[q] * qi;
+        xb[i] = pb[1] + 2.0 * x[i] * pb[3] + y[i] * pb[4];
+        yb[i] = pb[2] + x[i] * pb[4] + 2.0 * y[i] * pb[5];
+    }
+}
+
+// Minimal-image offset of slot s from the node, in FP64 from positions of type P.
+template <typename P>
+__device__ __forceinline__ void offset64(const void *pos, int s, double xn, double yn,
+                                         double &dx, double &dy)
+{
+    P px, py;
+    load_pos((const P *)pos, s, px, py);
+    dx = wrap1((double)px - xn);
+    dy = wrap1((double)py - yn);
+}
+
+template <typename P, typename V, typename R, int SHAPE, bool POS>
+__global__ void __launch_bounds__(64) k_bwd_fix(BwdArgs b)
+{
+    const P2MArgs &a = b.f;
+    const int cnt = min(*a.defer_count, a.defer_cap);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < cnt; it += gridDim.x * blockDim.x) {
+        const long long node = a.defer_list[it];
+        const int I = (int)(node % a.n), J = (int)(node / a.n);
+        const int nc = a.n - 1;
+        const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+        int *oslot = b.e_slot + node * b.K;
+        R *ow = (R *)b.e_w + node * b.K;
+        R *od = POS ? (R *)b.e_dpos + node * b.K * 2 : nullptr;
+        double g[8];
+        for (int c = 0; c < 8; ++c)
+            g[c] = c < a.C ? (double)load_val<V, R>((const V *)b.grad_mesh + node * a.C + c) : 0.0;
+        constexpr int UM = UMAX_SVD;
+        int us[UM];
+        double uw[UM], ub[UM], udx[UM], udy[UM];
+        int nu = 0, vi[3], tri[3];
+        unsigned vm[3] = {0u, 0u, 0u};
+        const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+        int stars[3][KMAX];
+        int ns[3] = {0, 0, 0};
+        int st = locate(a.B, qn, a.R0, tri, stars[0], ns[0]);
+        if (SHAPE == PFEM_SHAPE_QUADRATIC)
+            for (int e = 0; e < 3 && st == 0; ++e)
+                if (ns[e] == 0) {
+                    const int c = star_of(a.B, tri[e], a.R0, stars[e]);
+                    if (c < 0) st = c;
+                    else ns[e] = c;
+                }
+        if (st == 0) {
+            bool over = false;
+            auto add = [&](int s) -> int {
+                for (int i = 0; i < nu; ++i)
+                    if (us[i] == s) return i;
+                if (nu == UM || nu == b.K) { over = true; return 0; }
+                us[nu] = s;
+                uw[nu] = udx[nu] = udy[nu] = 0.0;
+                return nu++;
+            };
+            for (int e = 0; e < 3; ++e) vi[e] = add(tri[e]);
+            if (SHAPE == PFEM_SHAPE_QUADRATIC)
+                for (int e = 0; e < 3; ++e) {
+                    unsigned m = 1u << vi[e];
+                    for (int i = 0; i < ns[e]; ++i) m |= 1u << add(stars[e][i]);
+                    vm[e] = m;
+                }
+            if (over) st = -PFEM_ERR_CAPACITY;
+        }
+        if (st == 0) {
+            // offsets from the node in FP64 (FP32 positions promoted, as the forward fix pass does)
+            NodePos<P, R> np;
+            np.init(Iu, Ju, nc);
+            double ox[UM], oy[UM];
+            for (int i = 0; i < nu; ++i) {
+                R dx, dy;
+                np.off(a.pos, us[i], dx, dy);
+                ox[i] = (double)dx;
+                oy[i] = (double)dy;
+                R v[8];
+                load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
+                double t = 0.0;
+                for (int c = 0; c < 8; ++c)
+                    if (c < a.C) t = fma(g[c], (double)v[c], t);
+                ub[i] = t;
+            }
+            double d[3][2];
+            for (int e = 0; e < 3; ++e) { d[e][0] = ox[vi[e]]; d[e][1] = oy[vi[e]]; }
+            const double Na = d[1][0] * d[2][1] - d[1][1] * d[2][0];
+            const double Nb = d[2][0] * d[0][1] - d[2][1] * d[0][0];
+            const double Nc = d[0][0] * d[1][1] - d[0][1] * d[1][0];
+            const double A2 = Na + Nb + Nc;
+            const double lam[3] = {Na / A2, Nb / A2, Nc / A2};
+            double lbar[3];
+            for (int e = 0; e < 3; ++e) {
+                uw[vi[e]] += lam[e];
+                lbar[e] = ub[vi[e]];
+            }
+            if (SHAPE == PFEM_SHAPE_QUADRATIC)
+                for (int e = 0; e < 3; ++e) {
+                    const int f = e == 2 ? 0 : e + 1;
+                    const unsigned mask = vm[e] | vm[f];
+                    const double mx = 0.5 * (d[e][0] + d[f][0]), my = 0.5 * (d[e][1] + d[f][1]);
+                    const double ex = d[e][0] - d[f][0], ey = d[e][1] - d[f][1];
+                    const double sl = sqrt(ex * ex + ey * ey), inv = 1.0 / sl;
+                    const double tx = ex * inv, ty = ey * inv;
+                    double pt[UM][6], x[UM], y[UM], be[UM], A[UM], xb[UM], yb[UM];
+                    int ids[UM];
+                    int k = 0;
+                    for (unsigned m = mask; m; m &= m - 1) {
+                        const int i = __ffs(m) - 1;
+                        x[k] = (ox[i] - mx) * inv;
+                        y[k] = (oy[i] - my) * inv;
+                        pt[k][0] = 1.0; pt[k][1] = x[k]; pt[k][2] = y[k];
+                        pt[k][3] = x[k] * x[k]; pt[k][4] = x[k] * y[k]; pt[k][5] = y[k] * y[k];
+                        be[k] = ub[i];
+                        ids[k++] = i;
+                    }
+                    const double bv[6] = {0.0, 0.0, 0.0, -0.5 * tx * tx, -0.5 * tx * ty, -0.5 * ty * ty};
+                    const double ce = 2.0 * lam[e] * lam[f];
+                    double bb[6], Be;
+                    edge_adjoint_svd(k, pt, x, y, be, bv, ce, A, xb, yb, bb, Be);
+                    for (int j = 0; j < k; ++j) uw[ids[j]] = fma(ce, A[j], uw[ids[j]]);
+                    lbar[e] += 2.0 * lam[f] * Be;
+                    lbar[f] += 2.0 * lam[e] * Be;
+                    if (POS) {
+                        // members: x = (o - m) / s; frame: m = (d_e + d_f) / 2, s = |d_e - d_f|
+                        double mbx = 0.0, mby = 0.0, sb = 0.0;
+                        for (int j = 0; j < k; ++j) {
+                            udx[ids[j]] += xb[j] * inv;
+                            udy[ids[j]] += yb[j] * inv;
+                            mbx -= xb[j] * inv;
+                            mby -= yb[j] * inv;
+                            sb -= (xb[j] * x[j] + yb[j] * y[j]) * inv;
+                        }
+                        // b = -(1/2) [tx^2, tx ty, ty^2] with t = (d_e - d_f) / s
+                        const double tbx = -tx * bb[3] - 0.5 * ty * bb[4];
+                        const double tby = -0.5 * tx * bb[4] - ty * bb[5];
+                        const double tt = tbx * tx + tby * ty;
+                        const double ebx = (tbx - tt * tx) * inv + sb * tx;
+                        const double eby = (tby - tt * ty) * inv + sb * ty;
+                        udx[vi[e]] += 0.5 * mbx + ebx;
+                        udy[vi[e]] += 0.5 * mby + eby;
+                        udx[vi[f]] += 0.5 * mbx - ebx;
+                        udy[vi[f]] += 0.5 * mby - eby;
+                    }
+                }
+            if (POS) {
+                // lambda_k = N_k / A2 with N_a = d_b x d_c, N_b = d_c x d_a, N_c = d_a x d_b
+                const double Lam = lbar[0] * lam[0] + lbar[1] * lam[1] + lbar[2] * lam[2];
+                const double n0 = (lbar[0] - Lam) / A2, n1 = (lbar[1] - Lam) / A2,
+                             n2 = (lbar[2] - Lam) / A2;
+                double gx[3] = {0.0, 0.0, 0.0}, gy[3] = {0.0, 0.0, 0.0};
+                gx[1] += n0 * d[2][1];  gy[1] -= n0 * d[2][0];
+                gx[2] -= n0 * d[1][1];  gy[2] += n0 * d[1][0];
+                gx[2] += n1 * d[0][1];  gy[2] -= n1 * d[0][0];
+                gx[0] -= n1 * d[2][1];  gy[0] += n1 * d[2][0];
+                gx[0] += n2 * d[1][1];  gy[0] -= n2 * d[1][0];
+                gx[1] -= n2 * d[0][1];  gy[1] += n2 * d[0][0];
+                for (int e = 0; e < 3; ++e) {
+                    udx[vi[e]] += gx[e];
+                    udy[vi[e]] += gy[e];
+                }
+            }
+        }
+        if (st != 0) {
+            if (st == -PFEM_FAR) st = -PFEM_ERR_CAPACITY;
+            record_error(a.status, -st, node);
+            nu = 0;
+        }
+        for (int k = 0; k < b.K; ++k) {
+            const bool v = k < nu;
+            oslot[k] = v ? us[k] : -1;
+            ow[k] = v ? (R)uw[k] : R(0);
+            if (POS) {
+                od[2 * k] = v ? (R)udx[k] : R(0);
+                od[2 * k + 1] = v ? (R)udy[k] : R(0);
+            }
         }
     }
 }
@@ -417,6 +672,7 @@ BwdLayout bwd_layout(int n, long long N, int Kw)
     NodeRecs r;
     L.rec = off;     off = al(off + node_recs_layout(nullptr, (long long)n * n, &r));
     L.tab = off;     off = al(off + star_tab_bytes(N));
+    L.queue = off;   off = al(off + 8 * (size_t)n * n);
     L.total = off;
     return L;
 }
@@ -488,7 +744,12 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
     // the star table's queue counter sits in the status block, after the status word
     const StarTab tab = star_tab_layout(ws + L.tab, g.N, (int *)(ws + 64));
     const bool split = SHAPE == PFEM_SHAPE_QUADRATIC && sizeof(S) == sizeof(float);
+    // the fix-pass queue: its counter in the status block, one entry per node
+    b.f.defer_count = (int *)(ws + 68);
+    b.f.defer_list = (long long *)(ws + L.queue);
+    b.f.defer_cap = (int)std::min((long long)g.n * g.n, (long long)0x7fffffff);
     auto node_pass = [&](bool pos) {
+        cudaMemsetAsync(b.f.defer_count, 0, sizeof(int), s);
         if (split) {
             launch_star_table(b.f.B, g.R0, g.rmax_far, tab, b.f.status, s);
             k_p2m_geom<P, V, R><<<grid, 128, 0, s>>>(b.f, tab, recs);
@@ -501,6 +762,12 @@ static cudaError_t bwd_t(const GeoArgs &g, const int *perm, int C, const void *v
             else k_bwd_node<P, V, R, S, SHAPE, false><<<grid, 128, 0, s>>>(b);
             count_launch();
         }
+        // the queued nodes: widest search radius, FP64 SVD adjoint
+        BwdArgs bf = b;
+        bf.f.B.rmax = std::max(g.rmax, g.rmax_far);
+        if (pos) k_bwd_fix<P, V, R, SHAPE, true><<<num_sms() * 2, 64, 0, s>>>(bf);
+        else k_bwd_fix<P, V, R, SHAPE, false><<<num_sms() * 2, 64, 0, s>>>(bf);
+        count_launch();
     };
     if (checkpoint) {
         // value gradient straight from the stored weights

@@ -93,7 +93,7 @@ cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, in
 
 struct BwdLayout {
     int K;   // entries per node written by the recompute kernel
-    size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, rec, tab, total;   // rec: node records, tab: star table
+    size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, rec, tab, queue, total;   // rec: node records, tab: star table, queue: fix-pass nodes
 };
 BwdLayout bwd_layout(int n, long long N, int K);
 

@@ -60,14 +60,14 @@ __device__ __forceinline__ int defer_or_error(const P2MArgs &a, int st, long lon
 
 // Minimum-norm least-squares solution of P A = b (App. A: the SVD with rank detection), for the
 // 6 x k matrix P whose columns are the stencil's monomial vectors; pt holds P^T (k rows of 6)
-// and is overwritten.  One-sided (Hestenes) Jacobi: plane rotations of pairs of the six columns
-// of P^T until all are mutually orthogonal, accumulated in V, so that P^T V = W with orthogonal
-// columns w_j = sigma_j u_j.  Then P = V W^T and A = sum_j (v_j . b / sigma_j^2) w_j over the
-// singular values above max(k, 6) eps sigma_max (smaller ones are rank deficiency).
-static __device__ __noinline__ void minnorm_lsq(int k, double (*pt)[6], const double b[6],
-                                                double *A)
+// and is overwritten.  One-sided (Hestenes) Jacobi (jacobi_svd): plane rotations of pairs of the
+// six columns of P^T until all are mutually orthogonal, accumulated in V, so that P^T V = W with
+// orthogonal columns w_j = sigma_j u_j (left in pt) and sig2[j] = sigma_j^2.  Then P = V W^T and
+// A = sum_j (v_j . b / sigma_j^2) w_j over the singular values above max(k, 6) eps sigma_max
+// (smaller ones are rank deficiency).
+static __device__ __forceinline__ void jacobi_svd(int k, double (*pt)[6], double V[6][6],
+                                                  double sig2[6])
 {
-    double V[6][6];
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) V[i][j] = i == j ? 1.0 : 0.0;
     for (int sweep = 0; sweep < 40; ++sweep) {
@@ -98,17 +98,33 @@ static __device__ __noinline__ void minnorm_lsq(int k, double (*pt)[6], const do
             }
         if (!rotated) break;
     }
-    double sig2[6], vb[6], smax2 = 0.0;
     for (int j = 0; j < 6; ++j) {
-        double s2 = 0.0, d = 0.0;
+        double s2 = 0.0;
         for (int i = 0; i < k; ++i) s2 = fma(pt[i][j], pt[i][j], s2);
-        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
         sig2[j] = s2;
-        vb[j] = d;
-        smax2 = fmax(smax2, s2);
     }
+}
+
+// Squared singular values kept by the rank detection: above (max(k, 6) eps)^2 sigma_max^2.
+__device__ __forceinline__ double svd_threshold2(int k, const double sig2[6])
+{
+    double smax2 = 0.0;
+    for (int j = 0; j < 6; ++j) smax2 = fmax(smax2, sig2[j]);
     const double tol = (double)(k > 6 ? k : 6) * 2.220446049250313e-16;
-    const double thr2 = tol * tol * smax2;
+    return tol * tol * smax2;
+}
+
+static __device__ __noinline__ void minnorm_lsq(int k, double (*pt)[6], const double b[6],
+                                                double *A)
+{
+    double V[6][6], sig2[6], vb[6];
+    jacobi_svd(k, pt, V, sig2);
+    for (int j = 0; j < 6; ++j) {
+        double d = 0.0;
+        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
+        vb[j] = d;
+    }
+    const double thr2 = svd_threshold2(k, sig2);
     for (int i = 0; i < k; ++i) {
         double a = 0.0;
         for (int j = 0; j < 6; ++j)

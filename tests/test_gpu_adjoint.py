@@ -182,3 +182,34 @@ def test_gradient_workload_full_size_band(P):
     print("full-size band gradient error (vals, pos):", res)
     assert res["torch.float64"][0] <= 1e-12 and res["torch.float64"][1] <= 1e-12
     assert res["torch.float32"][0] < 1e-5 and res["torch.float32"][1] < 1e-2
+
+
+def test_uniform_random_gradient_takes_the_fix_pass(P):
+    """Uniform random particles (512^2 on the 257^2 mesh): the node rows 40..63 include node
+    (68, 52), whose edge stencil of five particles makes its system inconsistent (least
+    squares, rank 5), and edge systems too ill-conditioned for the fast FP32 solve.  Those nodes
+    go to the adjoint's fix pass (FP64, derivative of the SVD pseudo-inverse with the edge frame
+    differentiated); no device error.  The upstream gradient is non-zero on those rows only,
+    and every particle's value and position gradient is compared with the oracle's (complex
+    step through its own least-squares route): FP64 within 1e-11 (values 1e-12), FP32 values
+    within 1e-5 and positions within 1e-2 of the largest entry."""
+    n, M = 257, 512
+    N = M * M
+    pos = G.uniform01(G.SEED_BASE + 62, 2 * N).reshape(N, 2)
+    vals = G.taylor_green(pos)[:, :2].copy()
+    g = np.zeros((n, n, 2))
+    g[40:64] = np.random.default_rng(31).standard_normal((24, n, 2))
+    res = {}
+    for dt in (torch.float64, torch.float32):
+        p = pos if dt == torch.float64 else pos.astype(np.float32).astype(np.float64)
+        ov, op = O.p2m_backward(n, p, vals, g, shape=1, node_range=(40 * n, 64 * n))
+        proj = gpu_proj(P, n, p, 2, dt)
+        solve = P.PFEM_SOLVE_F64 if dt == torch.float64 else P.PFEM_SOLVE_F32
+        gv, gp = proj.backward(torch.tensor(vals, dtype=dt, device="cuda"),
+                               torch.tensor(g, dtype=dt, device="cuda"), solve=solve)
+        code, detail = proj.backward_status()
+        assert code == 0, (dt, detail)
+        res[str(dt)] = (relerr(gv.cpu().numpy(), ov), relerr(gp.cpu().numpy(), op))
+    print("uniform random gradient error (vals, pos):", res)
+    assert res["torch.float64"][0] <= 1e-12 and res["torch.float64"][1] <= 1e-11
+    assert res["torch.float32"][0] < 1e-5 and res["torch.float32"][1] < 1e-2
