@@ -297,6 +297,39 @@ pfem_status pfem_interp_m2p_backward(pfem_ctx *ctx, int32_t n, int32_t nb, int64
                                      const void *grad_vals, pfem_dtype val_t, void *grad_mesh,
                                      void *grad_pos, void *stream);
 
+/* ------------------------------------------------------------------ the projection loop
+ * Sec. 3.1 runs, on Zalesak's disk, a loop whose every step projects the field mesh ->
+ * particles (M2P), moves the particles one step with the midpoint velocity, rebuilds the
+ * particle shape functions and projects particles -> mesh (P2M).  These two calls are the
+ * steps between the projections. */
+
+/* Midpoint move (the scheme of Sec. 3.2): r_half = r + dt/2 u(r), r_new = r + dt u(r_half), with
+ * u interpolated from the mesh velocity field mesh_vel [n, n, 2] (pos_t, same layout as M2P's
+ * mesh values) by linear FE on the structured mesh (eq. m2p).  pos [N, 2] in any order,
+ * pos_out [N, 2] in the same order, wrapped into [0, 1).  No workspace, no device errors. */
+pfem_status pfem_advect_midpoint(pfem_ctx *ctx, int32_t n, int64_t N, const void *pos,
+                                 pfem_dtype pos_t, const void *mesh_vel, double dt, void *pos_out,
+                                 void *stream);
+
+/* Bytes of workspace pfem_update_cells needs. */
+size_t pfem_update_workspace_size(int32_t nb, int64_t N);
+
+/* Re-bin particles that moved since the binning (cell_start_old, perm_old, q_sorted_old) of
+ * pfem_build_cells or of an earlier call: pos [N, 2] are the new positions in original order;
+ * the outputs are exactly those of pfem_build_cells(pos) provided every particle's new bin is
+ * its old bin or one of the eight around it on the torus.  The new bins are filled from the
+ * old ones without atomics: the particles that end in bin b come from the 3 x 3 old bins around
+ * b, each in original-index order, so a particle's slot is the start of b plus the number of
+ * those particles with a smaller original index.  A particle that moved further records
+ * PFEM_ERR_CAPACITY in the status word of ws (detail: its original index) and the outputs are
+ * then not valid: call pfem_build_cells.  The new arrays must not alias the old ones.  No paper
+ * counterpart (the paper rebuilds a global triangulation, App. A). */
+pfem_status pfem_update_cells(pfem_ctx *ctx, int32_t nb, int64_t N, const void *pos,
+                              pfem_dtype pos_t, const int32_t *cell_start_old,
+                              const int32_t *perm_old, const uint32_t *q_sorted_old,
+                              int32_t *cell_start, int32_t *perm, void *pos_sorted,
+                              uint32_t *q_sorted, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------ batches
  * Many independent problems (their own mesh size, particle count and bins) processed in one
  * launch per stage.  The caller concatenates the problems: particles of problem p occupy rows

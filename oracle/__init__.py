@@ -17,6 +17,7 @@ from .oracle import (  # noqa: F401
     mesh_edge,
     p2m_backward,
     m2p_backward,
+    advect_midpoint,
     fixed_point,
     OracleError,
     KSTEN,

@@ -221,3 +221,14 @@ def m2p_backward(n: int, pos, mesh, grad_vals):
     gp = np.zeros((N, 2))
     _check(lib().or_m2p_backward(n, N, pos, C, mesh, gv, gm, gp), "m2p_backward")
     return gm.reshape(n, n, C), gp
+
+
+def advect_midpoint(n: int, pos, mesh_vel, dt: float) -> np.ndarray:
+    """One midpoint step (the scheme of Sec. 3.2; the move of the Sec. 3.1 loop on Zalesak's
+    disk) of particles in the velocity field mesh_vel [n, n, 2], interpolated by eq. (m2p) with
+    linear FE: r_half = r + dt/2 u(r), r_new = r + dt u(r_half), wrapped into [0, 1)."""
+    pos = _pos(pos)
+    u = m2p(n, pos, mesh_vel)
+    half = pos + 0.5 * dt * u
+    new = pos + dt * m2p(n, half, mesh_vel)
+    return new - np.floor(new)

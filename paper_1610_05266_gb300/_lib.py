@@ -60,6 +60,11 @@ SIGNATURES = {
                                              _p, _sz, _p]),
     "pfem_interp_m2p_backward": (ctypes.c_int, [_p, _i32, _i32, _i64, _p, ctypes.c_int, _p, _p, _i32,
                                                 _p, _p, ctypes.c_int, _p, _p, _p]),
+    "pfem_advect_midpoint": (ctypes.c_int, [_p, _i32, _i64, _p, ctypes.c_int, _p, ctypes.c_double,
+                                            _p, _p]),
+    "pfem_update_workspace_size": (_sz, [_i32, _i64]),
+    "pfem_update_cells": (ctypes.c_int, [_p, _i32, _i64, _p, ctypes.c_int, _p, _p, _p, _p, _p, _p,
+                                         _p, _p, _sz, _p]),
     "pfem_batch_plan_size": (_sz, [_i32]),
     "pfem_batch_plan_init": (ctypes.c_int, [_p, _i32, _p, _p, ctypes.POINTER(_i64)]),
     "pfem_batch_workspace_size": (_sz, [_i64, _i64, _i64]),

@@ -170,6 +170,25 @@ def pfem_interp_m2p_backward(n, nb, N, pos, cell_start, perm, C, mesh_vals, grad
           "pfem_interp_m2p_backward", ctx)
 
 
+def pfem_advect_midpoint(n, N, pos, mesh_vel, dt, pos_out, stream=None, ctx=None):
+    check(L.load().pfem_advect_midpoint(L.ctx_ptr(ctx), n, N, ptr(pos), dtype_code(pos.dtype),
+                                        ptr(mesh_vel), float(dt), ptr(pos_out), stream_ptr(stream)),
+          "pfem_advect_midpoint", ctx)
+
+
+def pfem_update_workspace_size(nb: int, N: int) -> int:
+    return int(L.load().pfem_update_workspace_size(nb, N))
+
+
+def pfem_update_cells(nb, N, pos, cell_start_old, perm_old, q_sorted_old, cell_start, perm,
+                      pos_sorted, q_sorted, ws, stream=None, ctx=None):
+    check(L.load().pfem_update_cells(L.ctx_ptr(ctx), nb, N, ptr(pos), dtype_code(pos.dtype),
+                                     ptr(cell_start_old), ptr(perm_old), ptr(q_sorted_old),
+                                     ptr(cell_start), ptr(perm), ptr(pos_sorted), ptr(q_sorted),
+                                     ptr(ws), _nbytes(ws), stream_ptr(stream)),
+          "pfem_update_cells", ctx)
+
+
 def pfem_batch_plan_size(P: int) -> int:
     return int(L.load().pfem_batch_plan_size(P))
 
@@ -342,6 +361,29 @@ class Projector:
                                  mesh.contiguous(), grad_vals.contiguous(), gm, gp, stream, ctx=self.ctx)
         return gm, gp
 
+    def advect(self, pos: torch.Tensor, mesh_vel: torch.Tensor, dt: float, out=None,
+               stream=None) -> torch.Tensor:
+        """Midpoint move of pos (any order) in the mesh velocity field mesh_vel [n, n, 2]."""
+        if out is None:
+            out = torch.empty_like(pos)
+        pfem_advect_midpoint(self.n, pos.shape[0], pos, mesh_vel.contiguous(), dt, out, stream,
+                             ctx=self.ctx)
+        return out
+
+    def update(self, pos: torch.Tensor, stream=None):
+        """Re-bin after a move of at most one bin per particle (pfem_update_cells): the new
+        binning goes to a second set of buffers, which then becomes the current one."""
+        c = self.cells
+        alt = getattr(self, "_alt", None)
+        if alt is None:
+            dev = self.device
+            alt = Cells(c.n, c.nb, c.N, torch.empty_like(c.cell_start), torch.empty_like(c.perm),
+                        torch.empty_like(c.pos_sorted), torch.empty_like(c.q_sorted), c.ws)
+        pfem_update_cells(self.nb, self.N, pos, c.cell_start, c.perm, c.q_sorted, alt.cell_start,
+                          alt.perm, alt.pos_sorted, alt.q_sorted, c.ws, stream, ctx=self.ctx)
+        self._alt, self.cells = c, alt
+        return alt
+
     def status(self, stream=None) -> Tuple[int, int]:
         return pfem_get_device_status(self.cells.ws, stream, ctx=self.ctx)
 
@@ -352,6 +394,26 @@ class Projector:
         code, detail = self.status(stream)
         if code != 0:
             raise PfemError(code, f"{what} (first failure at index {detail})")
+
+
+def projection_loop(proj: Projector, pos: torch.Tensor, mesh: torch.Tensor,
+                    mesh_vel: torch.Tensor, dt: float, steps: int,
+                    m2p_shape=PFEM_SHAPE_LINEAR, p2m_shape=PFEM_SHAPE_QUADRATIC, solve=None,
+                    incremental: bool = True, stream=None):
+    """The loop of Sec. 3.1 on Zalesak's disk: each step projects the mesh field onto the
+    particles (M2P), moves the particles one step with the midpoint velocity interpolated from
+    mesh_vel, re-bins them (the incremental update, or a full pfem_build_cells) and projects
+    the particle values back onto the mesh (P2M, shape functions rebuilt).  pos [N, 2] in
+    original order; proj must have been built for pos.  Returns (pos, mesh) after `steps`."""
+    for _ in range(steps):
+        vals = proj.m2p(pos, mesh, shape=m2p_shape, stream=stream)
+        pos = proj.advect(pos, mesh_vel, dt, stream=stream)
+        if incremental:
+            proj.update(pos, stream=stream)
+        else:
+            proj.build(pos, stream=stream)
+        mesh = proj.p2m(vals, shape=p2m_shape, solve=solve, stream=stream)
+    return pos, mesh
 
 
 class Batch:

@@ -491,6 +491,48 @@ pfem_status pfem_interp_m2p_backward(pfem_ctx *ctx, int32_t n, int32_t nb, int64
                                                 (cudaStream_t)stream), fn);
 }
 
+pfem_status pfem_advect_midpoint(pfem_ctx *ctx, int32_t n, int64_t N, const void *pos,
+                                 pfem_dtype pos_t, const void *mesh_vel, double dt, void *pos_out,
+                                 void *stream)
+{
+    const char *fn = "pfem_advect_midpoint";
+    if (n < 9 || N < 0 || N >= (1LL << 40)) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: n or N out of range", fn);
+    if (N > 0 && (!pos || !mesh_vel || !pos_out)) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: NULL buffer", fn);
+    if (pos_t != PFEM_F64 && pos_t != PFEM_F32) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: unknown pos_t", fn);
+    if (!(std::fabs(dt) < 1e30)) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: dt is not finite", fn);
+    if (N == 0) return ok(ctx);
+    return cuda_result(ctx, launch_advect_midpoint(n, N, pos, pos_t, mesh_vel, dt, pos_out,
+                                                   (cudaStream_t)stream), fn);
+}
+
+size_t pfem_update_workspace_size(int32_t nb, int64_t N)
+{
+    if (nb < 1 || N < 0) return 0;
+    return update_ws_bytes((long long)nb * nb, N);
+}
+
+pfem_status pfem_update_cells(pfem_ctx *ctx, int32_t nb, int64_t N, const void *pos,
+                              pfem_dtype pos_t, const int32_t *cell_start_old,
+                              const int32_t *perm_old, const uint32_t *q_sorted_old,
+                              int32_t *cell_start, int32_t *perm, void *pos_sorted,
+                              uint32_t *q_sorted, void *ws, size_t ws_bytes, void *stream)
+{
+    const char *fn = "pfem_update_cells";
+    if (nb < 3 || (long long)nb * nb >= (1LL << 30) || N < 0 || N >= (1LL << 31))
+        return say(ctx, PFEM_ERR_INVALID_ARG, "%s: nb = %d (>= 3) or N = %lld out of range", fn, nb, (long long)N);
+    if (!cell_start_old || !cell_start || !ws ||
+        (N > 0 && (!pos || !perm_old || !q_sorted_old || !perm || !pos_sorted || !q_sorted)))
+        return say(ctx, PFEM_ERR_INVALID_ARG, "%s: NULL buffer", fn);
+    if (cell_start == cell_start_old || perm == perm_old || q_sorted == q_sorted_old)
+        return say(ctx, PFEM_ERR_INVALID_ARG, "%s: the new arrays must not alias the old ones", fn);
+    if (pos_t != PFEM_F64 && pos_t != PFEM_F32) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: unknown pos_t", fn);
+    const size_t need = update_ws_bytes((long long)nb * nb, N);
+    if (ws_bytes < need) return say(ctx, PFEM_ERR_WORKSPACE, "%s: ws_bytes = %zu < %zu", fn, ws_bytes, need);
+    return cuda_result(ctx, launch_update_cells(nb, N, pos, pos_t, cell_start_old, perm_old,
+                                                q_sorted_old, cell_start, perm, pos_sorted,
+                                                q_sorted, ws, (cudaStream_t)stream), fn);
+}
+
 size_t pfem_batch_plan_size(int32_t P)
 {
     return P < 1 ? 0 : batch_plan_bytes(P);

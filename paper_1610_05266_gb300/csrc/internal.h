@@ -91,6 +91,14 @@ cudaError_t launch_m2p_quadratic(int n, long long N, const void *pos, pfem_dtype
 cudaError_t launch_m2p(int n, long long N, const void *pos, pfem_dtype pos_t, int C,
                        const void *mesh, void *vals, pfem_dtype val_t, cudaStream_t s);
 
+cudaError_t launch_advect_midpoint(int n, long long N, const void *pos, pfem_dtype pos_t,
+                                   const void *vel, double dt, void *out, cudaStream_t s);
+size_t update_ws_bytes(long long nbins, long long N);
+cudaError_t launch_update_cells(int nb, long long N, const void *pos, pfem_dtype pos_t,
+                                const int *start_old, const int *perm_old, const uint32_t *q_old,
+                                int *cell_start, int *perm, void *pos_sorted, uint32_t *q_sorted,
+                                void *ws, cudaStream_t s);
+
 struct BwdLayout {
     int K;   // entries per node written by the recompute kernel
     size_t e_slot, e_w, e_dpos, count, start, rank, order, scan, rec, tab, queue, total;   // rec: node records, tab: star table, queue: fix-pass nodes

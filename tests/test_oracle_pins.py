@@ -537,3 +537,38 @@ def test_mesh_qcsf_m2p_order_and_interpolation():
     mesh[:, -1] = mesh[:, 0]
     p = np.array([[5 / 16, 9 / 16]])
     assert np.abs(O.m2p_quadratic(n, p, mesh)[0] - mesh[9, 5]).max() < 1e-14
+
+
+# ------------------------------------------------------------------ the projection loop's move
+
+
+def test_midpoint_move_of_a_uniform_field_is_a_translation():
+    """A uniform mesh velocity is reproduced exactly by linear FE (eq. C1), so the midpoint
+    step is the exact translation r + dt u (Sec. 3.2 scheme), wrapped into the torus."""
+    n = 33
+    pos = G.uniform01(G.SEED_BASE + 500, 2000).reshape(1000, 2)
+    vel = np.zeros((n, n, 2))
+    vel[..., 0], vel[..., 1] = 0.37, -1.9
+    new = O.advect_midpoint(n, pos, vel, 0.05)
+    want = pos + 0.05 * np.array([0.37, -1.9])
+    want -= np.floor(want)
+    d = new - want
+    assert np.abs(d - np.rint(d)).max() < 1e-14
+
+
+def test_midpoint_move_of_a_rotation_is_second_order_taylor():
+    """Rigid rotation about the centre sampled at the nodes: away from the periodic seam the
+    field is linear, which linear FE reproduces exactly, so one midpoint step maps
+    r - c -> (I + dt A + (dt A)^2 / 2)(r - c) with A = omega [[0, -1], [1, 0]] (the midpoint
+    scheme's second-order Taylor map for a linear field).  A full step in place of the half step
+    would break this."""
+    n, om, dt = 65, 2 * np.pi, 0.01
+    g = np.arange(n) / (n - 1)
+    X, Y = np.meshgrid(g, g)
+    vel = np.stack([-om * (Y - 0.5), om * (X - 0.5)], -1)
+    pos = 0.2 + 0.6 * G.uniform01(G.SEED_BASE + 501, 4000).reshape(2000, 2)
+    new = O.advect_midpoint(n, pos, vel, dt)
+    A = om * np.array([[0.0, -1.0], [1.0, 0.0]])
+    T = np.eye(2) + dt * A + 0.5 * (dt * A) @ (dt * A)
+    want = 0.5 + (pos - 0.5) @ T.T
+    assert np.abs(new - want).max() < 1e-13
