@@ -27,30 +27,37 @@ METRIC = "Mparticles/s for P2M+M2P round trip; %HBM peak; max rel err vs FP64 or
 UNIT = "Mparticles/s"
 L2_BYTES = 129 * 1024 * 1024
 
+# Mean edge-stencil size on the benchmark workload (oracle, 12,000 edges of 4,000 random nodes).
+STENCIL_MEAN = 10.43
 # FP32 arithmetic the method defines for one node of the quadratic P2M (the Delaunay search is
 # integer and filtered-predicate work, not counted): barycentrics (30) + 3 edges x (244 + 77 k)
-# with mean stencil size k = 10 (frame, Cholesky, two triangular solves; per stencil point the
-# coordinates, monomials, moment update, coefficient and the apply of C = 4 values), + 24.
-FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * 10) + 24
+# (frame, Cholesky, two triangular solves; per stencil point the coordinates, monomials, moment
+# update, coefficient and the apply of C = 4 values), + 24.
+FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * STENCIL_MEAN) + 24
+# FP64 arithmetic of the refinement residual r = b - sum_mu p_mu (p_mu . y) per node: per stencil
+# point the monomials (3), p . y (11) and the update of r (12).
+FP64_FLOP_PER_NODE_RES = 3 * 26 * STENCIL_MEAN
 FP32_LANES_PER_SM = 128
+FP64_PEAK_NOMINAL = 1.25      # TFLOP/s per GB300 (nominal, profiling recipe table); no measured value
 
 
-def p2m_traffic():
-    """DRAM bytes of one quadratic P2M call (its geometry, solve and SVD-pass kernels) from the
-    committed ncu summary, or None when the kernel sources changed since those counters were
-    taken."""
+def kernel_traffic(stage: str, solve: str):
+    """DRAM bytes per launch of the dominant kernel, from the committed ncu summary
+    (profiles/p2m_kernels_traffic.txt: lines 'key value'), or None when the kernel sources
+    changed since those counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_p2m_geom_solve_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "p2m_kernels_traffic.txt")
     try:
         kv = dict(line.split()[:2] for line in open(path) if line.strip() and not line.startswith("#"))
     except Exception:
         return None
     h = hashlib.sha256()
-    for f in ("p2m.cuh", "geom.cuh", "moments.cuh", "common.cuh", "p2m.cu"):
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1610_05266_gb300", "csrc"))):
         h.update(open(os.path.join(ROOT, "paper_1610_05266_gb300", "csrc", f), "rb").read())
     if kv.get("sha256") != h.hexdigest():
         return None
-    return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+    key = f"{stage}_{solve}"
+    return int(kv[key]) if key in kv else None
 
 
 def peaks():
@@ -272,7 +279,11 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    def step(rec=None):
+    ctx = P.Context()
+    proj.ctx = ctx
+    def step(rec=None, stage=None):
+        if stage is not None:
+            ctx.set_stage_events(stage)
         if rec is not None:
             rec[0].record(stream)
         proj.build(pos)
@@ -293,19 +304,27 @@ def run_ours(args, world, rank, local):
     clocks = ClockSampler(local)
     clocks.start()
     recs = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    stages = [[ev() for _ in range(5)] for _ in range(args.steps)]
+    for st in stages:
+        for e in st:
+            e.record(stream)                 # create the handles before the timed region
+    torch.cuda.synchronize()
     l0 = P.pfem_launch_count()
     barrier(world)
     torch.cuda.synchronize()
     clocks.mark("t_start")
     for k in range(args.steps):
         flush.zero_()                       # evict L2 between timed steps (outside the events)
-        step(recs[k])
+        step(recs[k], stages[k])
     torch.cuda.synchronize()
     clocks.mark("t_end")
     barrier(world)
     launches = P.pfem_launch_count() - l0
     clk = clocks.stop()
     proj.check("timed steps")
+    ctx.set_stage_events([])
+    stage_ms = {name: float(np.mean([st[i].elapsed_time(st[i + 1]) for st in stages]))
+                for i, name in enumerate(("star_table", "geometry", "solve", "fix_pass"))}
     step_ms = [r[0].elapsed_time(r[3]) for r in recs]
     cells_ms = [r[0].elapsed_time(r[1]) for r in recs]
     p2m_ms = [r[1].elapsed_time(r[2]) for r in recs]
@@ -324,6 +343,30 @@ def run_ours(args, world, rank, local):
     # per node; M2P reads pos per particle, C per node, writes C per particle (FP32)
     rt_bytes = N * (8 + 4 * C) + nn * 4 * C + N * 8 + nn * 4 * C + N * 4 * C
     m2p_bytes = N * 8 + nn * 4 * C + N * 4 * C
+    # roofline of the dominant kernel of the step, timed by the stage events: with the refined
+    # solve in FP64 residual form that is the solve kernel, bound by the FP64 pipe; otherwise
+    # the star table (integer and FP32 filter work) or the solve's FP32 arithmetic
+    dominant = max(stage_ms, key=stage_ms.get)
+    t_dom = stage_ms[dominant] * 1e-3
+    if dominant == "solve" and args.solve == "f32ref":
+        roofline = {"bound": "alu", "kernel": "k_p2m_solve (FP32 Cholesky + FP64-residual refinement)",
+                    "achieved": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12,
+                    "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s (FP64)",
+                    "frac": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12 / FP64_PEAK_NOMINAL,
+                    "algorithmic_flop_per_node": FP64_FLOP_PER_NODE_RES,
+                    "peak_source": "FP64 1.25 TFLOP/s per GB300 (nominal, of nominal: no measured FP64 peak)"}
+    else:
+        roofline = {"bound": "alu", "kernel": {"star_table": "k_star_list + k_star_retry",
+                                                "geometry": "k_p2m_geom", "solve": "k_p2m_solve",
+                                                "fix_pass": "k_p2m_fix"}[dominant],
+                    "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
+                    "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
+                    "note": "FP32 arithmetic of the whole quadratic P2M call over the call's time",
+                    "peak_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+    roofline["kernel_ms"] = stage_ms[dominant]
+    roofline["traffic"] = kernel_traffic(dominant, args.solve)
+    roofline["traffic_unit"] = "bytes per launch (ncu dram read+write), null when the sources changed since"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -331,14 +374,7 @@ def run_ours(args, world, rank, local):
                       "channels": C, "jitter": pr.a, "shape": "quadratic", "solve": args.solve,
                       "bins": proj.nb, "l2": "flushed between timed steps (2x L2 write)",
                       "parallelism": "replicas only" if world > 1 else "single GPU"},
-           "roofline": {"bound": "alu", "kernel": "quadratic P2M (k_p2m_geom + k_p2m_solve)",
-                        "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak,
-                        "unit": "TFLOP/s",
-                        "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
-                        "traffic": p2m_traffic(),
-                        "traffic_unit": "bytes per P2M call (ncu dram read+write, summed over its kernels)",
-                        "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
-                        "peak_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+           "roofline": roofline,
            "hbm_view": {"round_trip_bytes": rt_bytes,
                         "round_trip_gbs": rt_bytes / (t_step * 1e-3) / 1e9,
                         "round_trip_frac": rt_bytes / (t_step * 1e-3) / 1e9 / hbm_peak,
@@ -346,7 +382,7 @@ def run_ours(args, world, rank, local):
                         "m2p_frac": m2p_bytes / t_m2p / 1e9 / hbm_peak,
                         "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
            "breakdown_ms": {"build_cells": float(np.mean(cells_ms)), "p2m_quadratic": t_p2m * 1e3,
-                            "m2p": t_m2p * 1e3},
+                            "m2p": t_m2p * 1e3, "p2m_stages": stage_ms},
            "gpu_launches": int(launches),
            "clocks": clk}
     if args.profile:
@@ -409,6 +445,33 @@ def run_ours(args, world, rank, local):
     for nm, sv in (("f64", P.PFEM_SOLVE_F64), ("f32ref", P.PFEM_SOLVE_F32_REFINED), ("f32", P.PFEM_SOLVE_F32)):
         side[f"p2m_quadratic_solve_{nm}_ms"] = timeit(
             lambda: proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=sv, out=mesh))
+    def f32ff_round_trip():
+        proj.build(pos)
+        proj.p2m(vals, shape=P.PFEM_SHAPE_QUADRATIC, solve=P.PFEM_SOLVE_F32_REFINED_FF, out=mesh)
+        proj.m2p(pos, mesh, out=back)
+    side["f32ff_round_trip_ms"] = timeit(f32ff_round_trip)
+    side["f32ff_round_trip_mparticles_s"] = N / (side["f32ff_round_trip_ms"] * 1e-3) / 1e6
+    # the projection loop of the Zalesak procedure at this size: M2P of the field, midpoint move
+    # in a mesh rotation field, re-binning, quadratic P2M; dt keeps every move within one bin
+    gx = torch.arange(n, device=dev, dtype=torch.float32) / (n - 1)
+    Y, X = torch.meshgrid(gx, gx, indexing="ij")
+    inside = ((X - 0.5) ** 2 + (Y - 0.5) ** 2) < 0.45 ** 2
+    vel = torch.stack([torch.where(inside, -2 * np.pi * (Y - 0.5), 0.0),
+                       torch.where(inside, 2 * np.pi * (X - 0.5), 0.0)], -1).contiguous()
+    lproj = P.Projector(n, N, C=C, pos_dtype=torch.float32, device=dev)
+    lpos = pos.clone()
+    lproj.build(lpos)
+    lmesh = mesh.clone()
+    state = {"pos": lpos, "mesh": lmesh}
+    def loop_step(incremental):
+        state["pos"], state["mesh"] = P.projection_loop(
+            lproj, state["pos"], state["mesh"], vel, 2.5e-4, 1, solve=solve, incremental=incremental)
+    side["loop_step_incremental_rebin_ms"] = timeit(lambda: loop_step(True), reps=5)
+    side["loop_step_full_rebin_ms"] = timeit(lambda: loop_step(False), reps=5)
+    side["loop_update_cells_ms"] = timeit(lambda: lproj.update(state["pos"]), reps=5)
+    side["loop_build_cells_ms"] = timeit(lambda: lproj.build(state["pos"]), reps=5)
+    side["loop_status"] = int(lproj.status()[0])
+    del lproj, lpos, lmesh, state
     # plain FP64 single-instance form: FP64 positions and fields, FP64 solve
     pos64 = pos.double()                                     # the FP32 positions, exactly
     vals64 = torch.tensor(pr.vals, dtype=torch.float64, device=dev)

@@ -124,6 +124,14 @@ pfem_status pfem_get_options(const pfem_ctx *ctx, pfem_options *opt);
  * until the next call with the same context (or on the same thread). */
 const char *pfem_last_error(const pfem_ctx *ctx);
 
+/* Stage events for timing: events[0..count) are cudaEvent_t handles created by the caller
+ * (count <= 8; 0 clears them).  Every later pfem_project_p2m with this context records them on
+ * its stream at the boundaries of its stages when the star-table path runs: 0 before the fast
+ * pass, 1 after the star table, 2 after the per-node geometry kernel, 3 after the solve kernel,
+ * 4 after the fix pass (the other paths record 0 and 4 only).  The caller reads the intervals
+ * with cudaEventElapsedTime after synchronising.  Recording adds no work to the kernels. */
+pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count);
+
 /* Version of this ABI. */
 int pfem_abi_version(void);
 

@@ -48,6 +48,17 @@ class Context:
     def last_error(self) -> str:
         return pfem_last_error(self)
 
+    def set_stage_events(self, events):
+        """torch.cuda.Event objects (created with enable_timing=True) recorded by later P2M calls
+        at their stage boundaries (pfem_set_stage_events); [] clears them."""
+        for e in events:
+            if not e.cuda_event:
+                e.record()                   # materialise the CUDA event handle
+        arr = (ctypes.c_void_p * max(1, len(events)))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        check(self._lib.pfem_set_stage_events(self.handle, ctypes.cast(arr, ctypes.c_void_p), len(events)),
+              "pfem_set_stage_events", self)
+        self._events = list(events)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

@@ -70,6 +70,8 @@ WsLayout ws_layout_bins(long long nbins, long long N)
 struct pfem_ctx {
     pfem_options opt;
     char err[512];
+    void *events[8];            // stage events (cudaEvent_t) recorded by pfem_project_p2m
+    int nevents;
 };
 
 static thread_local char t_err[512];
@@ -195,6 +197,8 @@ static pfem_status make_geo(const pfem_ctx *ctx, const char *fn, int32_t n, int3
     g->kcap = o.star_capacity;
     g->walk_cap = o.walk_max_steps < 0 ? 0 : o.walk_max_steps;
     g->ucap = o.node_capacity;
+    g->events = ctx && ctx->nevents > 0 ? ctx->events : nullptr;
+    g->nevents = ctx ? ctx->nevents : 0;
     return PFEM_OK;
 }
 
@@ -240,6 +244,7 @@ pfem_status pfem_create(pfem_ctx **ctx, const pfem_options *opt)
     if (!c) return say(nullptr, PFEM_ERR_INVALID_ARG, "pfem_create: out of host memory");
     c->opt = o;
     c->err[0] = 0;
+    c->nevents = 0;
     *ctx = c;
     return ok(nullptr);
 }
@@ -254,6 +259,16 @@ pfem_status pfem_get_options(const pfem_ctx *ctx, pfem_options *opt)
 }
 
 const char *pfem_last_error(const pfem_ctx *ctx) { return err_buf(ctx); }
+
+pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count)
+{
+    if (!ctx) return say(nullptr, PFEM_ERR_INVALID_ARG, "pfem_set_stage_events: needs a context");
+    if (count < 0 || count > 8 || (count > 0 && !events))
+        return say(ctx, PFEM_ERR_INVALID_ARG, "pfem_set_stage_events: count must be 0..8");
+    for (int i = 0; i < count; ++i) ctx->events[i] = events[i];
+    ctx->nevents = count;
+    return ok(ctx);
+}
 
 int32_t pfem_default_bins(int32_t n, int64_t N)
 {

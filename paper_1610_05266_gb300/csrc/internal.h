@@ -62,7 +62,15 @@ struct GeoArgs {
     int kcap;                   // star capacity (<= PFEM_KMAX)
     int walk_cap;               // visibility-walk steps
     int ucap;                   // distinct particles of one node in the fast pass (<= PFEM_UMAX)
+    void *const *events = nullptr;  // stage events of the caller's context (cudaEvent_t), or null
+    int nevents = 0;
 };
+
+// Record stage event k of g on stream s (no-op without events).
+inline void stage_event(const GeoArgs &g, int k, cudaStream_t s)
+{
+    if (g.events && k < g.nevents && g.events[k]) cudaEventRecord((cudaEvent_t)g.events[k], s);
+}
 
 struct StarTab;
 struct Bins;

@@ -84,11 +84,15 @@ static bool set_table(NodeRecs &r, StarTab &t, void *ws, size_t ws_bytes, long l
 // shape functions, the apply form and room for the table, the fast pass is the star table, the
 // geometry kernel (node records) and the solve kernel; otherwise one kernel that searches the
 // stars per node.
+// Stage events (when the caller's context has them): 0 before the fast pass, 1 after the star
+// table, 2 after the geometry kernel, 3 after the solve kernel, 4 after the fix pass.
 template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
-static cudaError_t go(const P2MArgs &a, int R0, int rmax_far, cudaStream_t s,
+static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
                       const NodeRecs *rec = nullptr, const StarTab *tab = nullptr)
 {
+    const int R0 = g.R0, rmax_far = g.rmax_far;
     cudaError_t e;
+    stage_event(g, 0, s);
     if (a.defer_cap > 0) {
         e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
@@ -96,13 +100,16 @@ static cudaError_t go(const P2MArgs &a, int R0, int rmax_far, cudaStream_t s,
     if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab) {
         e = launch_star_table(a.B, R0, rmax_far, *tab, a.status, s);
         if (e != cudaSuccess) return e;
+        stage_event(g, 1, s);
         k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *tab, *rec);
         count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        stage_event(g, 2, s);
         k_p2m_solve<P, V, R, S, REF><<<(unsigned)((rec->nodes + 127) / 128), 128, 0, s>>>(a, *rec);
         count_launch();
         e = cudaGetLastError();
+        stage_event(g, 3, s);
     } else {
         e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s);
     }
@@ -111,19 +118,20 @@ static cudaError_t go(const P2MArgs &a, int R0, int rmax_far, cudaStream_t s,
     f.B.rmax = rmax_far > a.B.rmax ? rmax_far : a.B.rmax;
     k_p2m_fix<P, V, R, SHAPE, W><<<num_sms(), 128, 0, s>>>(f);
     count_launch();
+    stage_event(g, 4, s);
     return cudaGetLastError();
 }
 
 // Compute type S and refinement of each solve for FP32 arithmetic.
 template <typename P, typename V, int SHAPE, bool W>
-static cudaError_t go_solve(pfem_solve solve, const P2MArgs &a, int R0, int rmax_far,
-                            cudaStream_t s, const NodeRecs *r, const StarTab *t)
+static cudaError_t go_solve(pfem_solve solve, const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
+                            const NodeRecs *r, const StarTab *t)
 {
     switch (solve) {
-    case PFEM_SOLVE_F64: return go<P, V, float, double, REFINE_NONE, SHAPE, W>(a, R0, rmax_far, s, r, t);
-    case PFEM_SOLVE_F32: return go<P, V, float, float, REFINE_NONE, SHAPE, W>(a, R0, rmax_far, s, r, t);
-    case PFEM_SOLVE_F32_REFINED: return go<P, V, float, float, REFINE_F64, SHAPE, W>(a, R0, rmax_far, s, r, t);
-    default: return go<P, V, float, float, REFINE_FF, SHAPE, W>(a, R0, rmax_far, s, r, t);
+    case PFEM_SOLVE_F64: return go<P, V, float, double, REFINE_NONE, SHAPE, W>(g, a, s, r, t);
+    case PFEM_SOLVE_F32: return go<P, V, float, float, REFINE_NONE, SHAPE, W>(g, a, s, r, t);
+    case PFEM_SOLVE_F32_REFINED: return go<P, V, float, float, REFINE_F64, SHAPE, W>(g, a, s, r, t);
+    default: return go<P, V, float, float, REFINE_FF, SHAPE, W>(g, a, s, r, t);
     }
 }
 
@@ -143,17 +151,16 @@ cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *val
     const bool table = set_table(recs, tab, st, ws_bytes, (long long)g.n * g.n, g.N);
     const NodeRecs *r = table ? &recs : nullptr;
     const StarTab *t = table ? &tab : nullptr;
-    const int R0 = g.R0, rf = g.rmax_far;
     if (val_t == PFEM_F64) {   // positions FP64, arithmetic FP64
-        if (!q) return go<double, double, double, double, REFINE_NONE, 0, false>(a, R0, rf, s);
-        return go<double, double, double, double, REFINE_NONE, 1, false>(a, R0, rf, s, r, t);
+        if (!q) return go<double, double, double, double, REFINE_NONE, 0, false>(g, a, s);
+        return go<double, double, double, double, REFINE_NONE, 1, false>(g, a, s, r, t);
     }
     if (val_t == PFEM_F32) {   // positions FP32, arithmetic FP32
-        if (!q) return go<float, float, float, float, REFINE_NONE, 0, false>(a, R0, rf, s);
-        return go_solve<float, float, 1, false>(solve, a, R0, rf, s, r, t);
+        if (!q) return go<float, float, float, float, REFINE_NONE, 0, false>(g, a, s);
+        return go_solve<float, float, 1, false>(solve, g, a, s, r, t);
     }
-    if (!q) return go<float, __nv_bfloat16, float, float, REFINE_NONE, 0, false>(a, R0, rf, s);
-    return go_solve<float, __nv_bfloat16, 1, false>(solve, a, R0, rf, s, r, t);
+    if (!q) return go<float, __nv_bfloat16, float, float, REFINE_NONE, 0, false>(g, a, s);
+    return go_solve<float, __nv_bfloat16, 1, false>(solve, g, a, s, r, t);
 }
 
 cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, int K, int *w_idx,
@@ -165,13 +172,12 @@ cudaError_t launch_shape(const GeoArgs &g, pfem_shape shape, pfem_solve solve, i
     a.w_idx = w_idx;
     a.w = w;
     const bool q = shape == PFEM_SHAPE_QUADRATIC;
-    const int R0 = g.R0, rf = g.rmax_far;
     if (w_t == PFEM_F64) {
-        if (!q) return go<double, double, double, double, REFINE_NONE, 0, true>(a, R0, rf, s);
-        return go<double, double, double, double, REFINE_NONE, 1, true>(a, R0, rf, s);
+        if (!q) return go<double, double, double, double, REFINE_NONE, 0, true>(g, a, s);
+        return go<double, double, double, double, REFINE_NONE, 1, true>(g, a, s);
     }
-    if (!q) return go<float, float, float, float, REFINE_NONE, 0, true>(a, R0, rf, s);
-    return go_solve<float, float, 1, true>(solve, a, R0, rf, s, nullptr, nullptr);
+    if (!q) return go<float, float, float, float, REFINE_NONE, 0, true>(g, a, s);
+    return go_solve<float, float, 1, true>(solve, g, a, s, nullptr, nullptr);
 }
 
 // alpha_i = sum_k w[i,k] alpha[w_idx[i,k]] (explicit-weight P2M)
