@@ -19,11 +19,35 @@ namespace pfem {
 
 struct StarTab {
     int *nbr;           // [N][KMAX] slots
-    int *cnt;           // [N] star size (>= 3), -1 while queued, or -PFEM_ERR_*
+    int *cnt;           // [N] stamped count (tab_pack): star size, -1 while queued, or -PFEM_ERR_*
     int *queue;         // [N] slots whose list attempt failed
     int *qcount;        // number of queued slots
     long long N;
+    unsigned gen;       // stamp of this call's entries (1 .. 2^24 - 1)
+    // Slots whose stars are complete, [lo, hi) cyclically; hi < 0: all.  A pipelined call
+    // reads only these (the rest may still be being written by a concurrent kernel).
+    int lo = 0, hi = -1;
 };
+
+__device__ __forceinline__ bool tab_ready(const StarTab &t, int v)
+{
+    if (t.hi < 0) return true;
+    return t.lo <= t.hi ? (v >= t.lo && v < t.hi) : (v >= t.lo || v < t.hi);
+}
+
+// A count entry carries the stamp of the call that wrote it, so that an entry left by an
+// earlier call (or not yet written by this one) reads as "not available" (-1) instead of as a
+// star: (gen << 8) | (value + 128).
+__device__ __forceinline__ int tab_pack(unsigned gen, int v)
+{
+    return (int)((gen << 8) | (unsigned)((v + 128) & 255));
+}
+
+__device__ __forceinline__ int tab_count(const StarTab &t, int v)
+{
+    const unsigned w = (unsigned)__ldg(t.cnt + v);
+    return (w >> 8) == t.gen ? (int)(w & 255u) - 128 : -1;
+}
 
 // Star of slot v read from the table (entries through the read-only cache).
 struct TabStar {
@@ -34,7 +58,7 @@ struct TabStar {
 
 __device__ __forceinline__ TabStar tab_star(const StarTab &t, int v)
 {
-    return {t.nbr + (long long)v * KMAX, __ldg(t.cnt + v)};
+    return {t.nbr + (long long)v * KMAX, tab_ready(t, v) ? tab_count(t, v) : -1};
 }
 
 // Apex of the Delaunay triangle to the left of the directed edge u -> w: the neighbour that
@@ -57,7 +81,7 @@ static __device__ __noinline__ int locate_tab(const Bins &B, const StarTab &t, u
     const int v0 = nearest_particle(B, p, R0);
     if (v0 < 0) return v0;
     const TabStar s0 = tab_star(t, v0);
-    if (s0.n < 0) return s0.n;
+    if (s0.n < 0) return s0.n == -1 ? -PFEM_FAR : s0.n;
     return fan_walk(B, p, v0, s0, s0.n, [&](int u, int w) { return tab_apex(t, u, w); }, tri);
 }
 
@@ -302,11 +326,11 @@ __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const Star
         c = star_hull(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
                                [&](int k, int s) { out[k] = s; });
     if (c == -1) {
-        t.cnt[v] = -1;
+        t.cnt[v] = tab_pack(t.gen, -1);
         t.queue[atomicAdd(t.qcount, 1)] = (int)v;   // at most N entries: each slot once
         return;
     }
-    t.cnt[v] = c;
+    t.cnt[v] = tab_pack(t.gen, c);
     if (c < 0) record_error(st, -c, v);
 }
 
@@ -324,7 +348,7 @@ __device__ __forceinline__ void star_retry_slot(const Bins &B, int R0, const Sta
         if (c == -PFEM_FAR || c == -1) c = -PFEM_ERR_CAPACITY;
         record_error(st, -c, v);
     }
-    t.cnt[v] = c;
+    t.cnt[v] = tab_pack(t.gen, c);
 }
 
 }  // namespace pfem
