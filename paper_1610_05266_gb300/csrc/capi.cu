@@ -150,7 +150,7 @@ static const char *check_options(const pfem_options &o)
     if (o.batch_p2m_blocks < 0 || o.batch_m2p_blocks < 0) return "block counts must be >= 0";
     if (o.pipeline_chunks < 0 || o.pipeline_chunks > GeoArgs::MAX_CHUNKS)
         return "pipeline_chunks must be 0 (default) or 1..16";
-    for (int i = 0; i < 9; ++i)
+    for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return "reserved fields must be zero";
     return nullptr;
 }
