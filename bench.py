@@ -279,7 +279,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    ctx = P.Context(pipeline_chunks=args.chunks)
+    ctx = P.Context()
     proj.ctx = ctx
     def step(rec=None, stage=None):
         if stage is not None:
@@ -323,13 +323,8 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     proj.check("timed steps")
     ctx.set_stage_events([])
-    pipelined = ctx.options()["pipeline_chunks"] > 1
-    if pipelined:       # overlapping stages: the pipelined fast pass, then the fix pass
-        stage_ms = {"fast_pass_pipelined": float(np.mean([st[0].elapsed_time(st[3]) for st in stages])),
-                    "fix_pass": float(np.mean([st[3].elapsed_time(st[4]) for st in stages]))}
-    else:
-        stage_ms = {name: float(np.mean([st[i].elapsed_time(st[i + 1]) for st in stages]))
-                    for i, name in enumerate(("star_table", "geometry", "solve", "fix_pass"))}
+    stage_ms = {name: float(np.mean([st[i].elapsed_time(st[i + 1]) for st in stages]))
+                for i, name in enumerate(("star_table", "geometry", "solve", "fix_pass"))}
     step_ms = [r[0].elapsed_time(r[3]) for r in recs]
     cells_ms = [r[0].elapsed_time(r[1]) for r in recs]
     p2m_ms = [r[1].elapsed_time(r[2]) for r in recs]
@@ -353,16 +348,7 @@ def run_ours(args, world, rank, local):
     # the star table (integer and FP32 filter work) or the solve's FP32 arithmetic
     dominant = max(stage_ms, key=stage_ms.get)
     t_dom = stage_ms[dominant] * 1e-3
-    if dominant == "fast_pass_pipelined" and args.solve == "f32ref":
-        roofline = {"bound": "alu",
-                    "kernel": "quadratic P2M fast pass, pipelined (k_star_list/k_p2m_geom/k_p2m_solve "
-                              "on three streams; FP64 pipe of the refinement residual binding)",
-                    "achieved": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12,
-                    "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s (FP64)",
-                    "frac": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12 / FP64_PEAK_NOMINAL,
-                    "algorithmic_flop_per_node": FP64_FLOP_PER_NODE_RES,
-                    "peak_source": "FP64 1.25 TFLOP/s per GB300 (nominal, of nominal: no measured FP64 peak)"}
-    elif dominant == "solve" and args.solve == "f32ref":
+    if dominant == "solve" and args.solve == "f32ref":
         roofline = {"bound": "alu", "kernel": "k_p2m_solve (FP32 Cholesky + FP64-residual refinement)",
                     "achieved": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12,
                     "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s (FP64)",
@@ -372,8 +358,7 @@ def run_ours(args, world, rank, local):
     else:
         roofline = {"bound": "alu", "kernel": {"star_table": "k_star_list + k_star_retry",
                                                 "geometry": "k_p2m_geom", "solve": "k_p2m_solve",
-                                                "fix_pass": "k_p2m_fix",
-                                                "fast_pass_pipelined": "quadratic P2M fast pass, pipelined"}[dominant],
+                                                "fix_pass": "k_p2m_fix"}[dominant],
                     "achieved": p2m_flops / t_p2m / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": p2m_flops / t_p2m / 1e12 / fp32_peak,
                     "algorithmic_flop_per_node": FLOP_PER_NODE_Q,
@@ -707,8 +692,6 @@ def main():
                          "refinement step with an FP64 residual (default); f32ff = the same with "
                          "a float-float residual; f64 = FP64 assembly and solve; f32 = plain FP32 "
                          "Cholesky (a side variant outside the stated accuracy target)")
-    ap.add_argument("--chunks", type=int, default=0,
-                    help="pipeline chunks of the quadratic P2M (0: the library default, 1: off)")
     ap.add_argument("--profile", action="store_true", help="timed loop only (for ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle", action="store_true")

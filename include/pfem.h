@@ -101,16 +101,7 @@ typedef struct {
     int32_t batch_tile_rows;   /* node rows (4, 8, 16) of a batched P2M work item (default 8) */
     int32_t batch_p2m_blocks;  /* blocks of the persistent batched P2M (default 8 per SM) */
     int32_t batch_m2p_blocks;  /* blocks of the batched M2P (default 16 per SM) */
-    int32_t pipeline_chunks;   /* quadratic P2M with a context: node rows split into this many
-                                  chunks (2..16, default 8) whose star table, geometry and solve
-                                  kernels run on three streams, each chunk's FP64-heavy solve
-                                  overlapping the next chunks' integer-heavy geometry; 1 runs
-                                  the stages one after the other.  The context creates its two
-                                  extra streams and its events on the device current at its first
-                                  quadratic P2M call (make that call before any stream capture);
-                                  calls on another device run unpipelined.  Same results either
-                                  way. */
-    int32_t reserved[8];       /* zero */
+    int32_t reserved[9];       /* zero */
 } pfem_options;
 
 typedef struct pfem_ctx pfem_ctx;
@@ -137,8 +128,7 @@ const char *pfem_last_error(const pfem_ctx *ctx);
  * (count <= 8; 0 clears them).  Every later pfem_project_p2m with this context records them on
  * its stream at the boundaries of its stages when the star-table path runs: 0 before the fast
  * pass, 1 after the star table, 2 after the per-node geometry kernel, 3 after the solve kernel,
- * 4 after the fix pass (the other paths record 0 and 4 only; the pipelined path records 1, 2 and
- * 3 together when its overlapping stages are done).  The caller reads the intervals
+ * 4 after the fix pass (the other paths record 0 and 4 only).  The caller reads the intervals
  * with cudaEventElapsedTime after synchronising.  Recording adds no work to the kernels. */
 pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count);
 

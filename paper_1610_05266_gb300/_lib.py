@@ -84,8 +84,7 @@ class Options(ctypes.Structure):
     _fields_ = [("walk_max_steps", ctypes.c_int32), ("star_capacity", ctypes.c_int32),
                 ("node_capacity", ctypes.c_int32), ("search_radius_max", ctypes.c_int32),
                 ("batch_tile_rows", ctypes.c_int32), ("batch_p2m_blocks", ctypes.c_int32),
-                ("batch_m2p_blocks", ctypes.c_int32), ("pipeline_chunks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("batch_m2p_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class BatchProblem(ctypes.Structure):

@@ -410,7 +410,7 @@ class Projector:
 def projection_loop(proj: Projector, pos: torch.Tensor, mesh: torch.Tensor,
                     mesh_vel: torch.Tensor, dt: float, steps: int,
                     m2p_shape=PFEM_SHAPE_LINEAR, p2m_shape=PFEM_SHAPE_QUADRATIC, solve=None,
-                    incremental: bool = True, stream=None):
+                    incremental: bool = False, stream=None):
     """The loop of Sec. 3.1 on Zalesak's disk: each step projects the mesh field onto the
     particles (M2P), moves the particles one step with the midpoint velocity interpolated from
     mesh_vel, re-bins them (the incremental update, or a full pfem_build_cells) and projects

@@ -72,26 +72,7 @@ struct pfem_ctx {
     char err[512];
     void *events[8];            // stage events (cudaEvent_t) recorded by pfem_project_p2m
     int nevents;
-    // pipelined P2M: two streams and their events, created on device `dev` at first use
-    int dev = -1;
-    cudaStream_t streams[2] = {nullptr, nullptr};
-    cudaEvent_t pev[2 + 2 * GeoArgs::MAX_CHUNKS] = {};
 };
-
-// The context's pipeline objects on the current device (created at first use); false when the
-// context belongs to another device or they cannot be created.
-static bool ctx_pipeline(pfem_ctx *c)
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (c->dev >= 0) return c->dev == dev;
-    for (int i = 0; i < 2; ++i)
-        if (cudaStreamCreateWithFlags(&c->streams[i], cudaStreamNonBlocking) != cudaSuccess) return false;
-    for (auto &e : c->pev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
-    c->dev = dev;
-    return true;
-}
 
 static thread_local char t_err[512];
 
@@ -124,7 +105,6 @@ static void fill_defaults(pfem_options *o)
     if (o->star_capacity == 0) o->star_capacity = PFEM_KMAX;
     if (o->node_capacity == 0) o->node_capacity = PFEM_UMAX;
     if (o->batch_tile_rows == 0) o->batch_tile_rows = 8;
-    if (o->pipeline_chunks == 0) o->pipeline_chunks = 8;
 }
 
 static pfem_options opts_of(const pfem_ctx *c)
@@ -148,8 +128,6 @@ static const char *check_options(const pfem_options &o)
         o.batch_tile_rows != 16)
         return "batch_tile_rows must be 0 (default), 4, 8 or 16";
     if (o.batch_p2m_blocks < 0 || o.batch_m2p_blocks < 0) return "block counts must be >= 0";
-    if (o.pipeline_chunks < 0 || o.pipeline_chunks > GeoArgs::MAX_CHUNKS)
-        return "pipeline_chunks must be 0 (default) or 1..16";
     for (size_t i = 0; i < sizeof(o.reserved) / sizeof(o.reserved[0]); ++i)
         if (o.reserved[i] != 0) return "reserved fields must be zero";
     return nullptr;
@@ -271,21 +249,7 @@ pfem_status pfem_create(pfem_ctx **ctx, const pfem_options *opt)
     return ok(nullptr);
 }
 
-void pfem_destroy(pfem_ctx *ctx)
-{
-    if (!ctx) return;
-    if (ctx->dev >= 0) {
-        int cur = 0;
-        const bool have = cudaGetDevice(&cur) == cudaSuccess;
-        cudaSetDevice(ctx->dev);
-        for (auto &s : ctx->streams)
-            if (s) cudaStreamDestroy(s);
-        for (auto &e : ctx->pev)
-            if (e) cudaEventDestroy(e);
-        if (have) cudaSetDevice(cur);
-    }
-    delete ctx;
-}
+void pfem_destroy(pfem_ctx *ctx) { delete ctx; }
 
 pfem_status pfem_get_options(const pfem_ctx *ctx, pfem_options *opt)
 {
@@ -446,13 +410,6 @@ pfem_status pfem_project_p2m(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N,
         return say(ctx, PFEM_ERR_INVALID_ARG, "%s: FP64 values need FP64 positions and the FP64 solve", fn);
     if (val_t != PFEM_F64 && pos_t != PFEM_F32)
         return say(ctx, PFEM_ERR_INVALID_ARG, "%s: FP32 and BF16 values need FP32 positions", fn);
-    const int chunks = opts_of(ctx).pipeline_chunks;
-    if (ctx && chunks > 1 && shape == PFEM_SHAPE_QUADRATIC && ctx_pipeline(ctx)) {
-        g.chunks = chunks;
-        g.streams[0] = ctx->streams[0];
-        g.streams[1] = ctx->streams[1];
-        for (int i = 0; i < 2 + 2 * GeoArgs::MAX_CHUNKS; ++i) g.pev[i] = ctx->pev[i];
-    }
     return cuda_result(ctx, launch_p2m(g, perm, C, vals, val_t, shape, solve, mesh_vals,
                                        (DevStatus *)ws, ws_bytes, s), fn);
 }

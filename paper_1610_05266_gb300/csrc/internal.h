@@ -64,11 +64,6 @@ struct GeoArgs {
     int ucap;                   // distinct particles of one node in the fast pass (<= PFEM_UMAX)
     void *const *events = nullptr;  // stage events of the caller's context (cudaEvent_t), or null
     int nevents = 0;
-    // Pipelined quadratic P2M (the context's streams and events), chunks > 1 when enabled.
-    static constexpr int MAX_CHUNKS = 16;
-    int chunks = 1;
-    cudaStream_t streams[2] = {nullptr, nullptr};
-    cudaEvent_t pev[2 + 2 * MAX_CHUNKS] = {};   // begin, end, star chunk done[16], geometry done[16]
 };
 
 // Record stage event k of g on stream s (no-op without events).
@@ -86,8 +81,7 @@ unsigned next_tab_gen();
 StarTab star_tab_layout(char *base, long long N, int *qcount);
 cudaError_t launch_star_table(const Bins &B, int R0, int rmax_far, const StarTab &t,
                               DevStatus *st, cudaStream_t s);
-cudaError_t launch_star_rows(const Bins &B, int R0, int rmax_far, const StarTab &t, DevStatus *st,
-                             int row0, int row1, int *qc, cudaStream_t s);
+
 
 cudaError_t launch_p2m(const GeoArgs &g, const int *perm, int C, const void *vals,
                        pfem_dtype val_t, pfem_shape shape, pfem_solve solve, void *out,

@@ -84,69 +84,6 @@ static bool set_table(NodeRecs &r, StarTab &t, void *ws, size_t ws_bytes, long l
 // shape functions, the apply form and room for the table, the fast pass is the star table, the
 // geometry kernel (node records) and the solve kernel; otherwise one kernel that searches the
 // stars per node.
-// The table path pipelined over g.chunks chunks of node rows.  Chunk c's star table covers the
-// particles of the bin rows under its node rows; its geometry reads only the stars of chunks
-// c-1, c, c+1 (a node's triangle and the stars of its vertices lie within a bin row or two of
-// it; a walk that strays further finds "not ready" and sends the node to the fix pass), and its
-// solve runs on a third stream.  Three streams: the star tables in the order K-1, 0, 1, ..., K-2
-// on streams[0]; the geometry kernels on the caller's stream, chunk c after the star table of
-// chunk c+1 (all of them for the last two chunks); the solves on streams[1], chunk c after its
-// geometry.  The solves (FP64-pipe bound with the FP64-residual refinement) overlap the later
-// chunks' integer and FP32 work.  The caller's stream waits for the last solve, then runs the
-// fix pass.  Same kernels, same per-node arithmetic: the results are those of the sequential path.
-template <typename P, typename V, typename R, typename S, int REF>
-static cudaError_t go_pipelined(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
-                                const NodeRecs &rec, const StarTab &tab)
-{
-    const int K = g.chunks, n = a.n, nb = a.B.nb, nc = n - 1;
-    cudaStream_t S0 = g.streams[0], S1 = g.streams[1];
-    cudaEvent_t ev_begin = g.pev[0], ev_end = g.pev[1];
-    const cudaEvent_t *ev_star = g.pev + 2, *ev_geom = g.pev + 2 + GeoArgs::MAX_CHUNKS;
-    int J[GeoArgs::MAX_CHUNKS + 1], by[GeoArgs::MAX_CHUNKS + 1];
-    for (int c = 0; c <= K; ++c) {
-        J[c] = (int)((long long)c * nc / K);
-        by[c] = (int)((long long)J[c] * nb / nc);
-    }
-    J[K] = n;                                   // the last chunk takes the image row too
-    by[K] = nb;
-    int *qc = (int *)((char *)a.status + 264);  // one star-queue counter per chunk
-    cudaError_t e = cudaMemsetAsync(qc, 0, sizeof(int) * K, s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(ev_begin, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(S0, ev_begin, 0)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(S1, ev_begin, 0)) != cudaSuccess) return e;
-    for (int i = 0; i < K; ++i) {
-        const int c = i == 0 ? K - 1 : i - 1;
-        e = launch_star_rows(a.B, g.R0, g.rmax_far, tab, a.status, by[c], by[c + 1], qc + c, S0);
-        if (e != cudaSuccess) return e;
-        if ((e = cudaEventRecord(ev_star[i], S0)) != cudaSuccess) return e;
-    }
-    for (int c = 0; c < K; ++c) {
-        const int wait = c + 2 < K ? c + 2 : K - 1;      // execution index of chunk c+1's table
-        if ((e = cudaStreamWaitEvent(s, ev_star[wait], 0)) != cudaSuccess) return e;
-        int lo = 0, hi = -1;                             // ready bin rows: chunks c-1, c, c+1
-        if (c + 2 < K) {
-            lo = by[c == 0 ? K - 1 : c - 1];
-            hi = by[c + 2];
-        }
-        const dim3 grid((n + 15) / 16, (J[c + 1] - J[c] + 7) / 8);
-        k_p2m_geom<P, V, R><<<grid, 128, 0, s>>>(a, tab, rec, J[c], J[c + 1], lo, hi);
-        count_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(ev_geom[c], s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(S1, ev_geom[c], 0)) != cudaSuccess) return e;
-        const long long n0 = (long long)J[c] * n, n1 = (long long)J[c + 1] * n;
-        k_p2m_solve<P, V, R, S, REF><<<(unsigned)((n1 - n0 + 127) / 128), 128, 0, S1>>>(a, rec, n0, n1);
-        count_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if ((e = cudaEventRecord(ev_end, S1)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(s, ev_end, 0)) != cudaSuccess) return e;
-    // the stages overlap: stage events 1, 2 and 3 all mark the end of the pipelined fast pass
-    for (int k = 1; k <= 3; ++k) stage_event(g, k, s);
-    return cudaSuccess;
-}
-
 // Stage events (when the caller's context has them): 0 before the fast pass, 1 after the star
 // table, 2 after the geometry kernel, 3 after the solve kernel, 4 after the fix pass.
 template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
@@ -160,10 +97,7 @@ static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
         e = cudaMemsetAsync(a.defer_count, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab && g.chunks > 1 && a.B.nb >= 4 * g.chunks &&
-        a.n >= 8 * g.chunks) {
-        e = go_pipelined<P, V, R, S, REF>(g, a, s, *rec, *tab);
-    } else if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab) {
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab) {
         e = launch_star_table(a.B, R0, rmax_far, *tab, a.status, s);
         if (e != cudaSuccess) return e;
         stage_event(g, 1, s);

@@ -673,23 +673,13 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const StarTab &t, co
     }
 }
 
-// Node rows [J0, J1) (blockIdx.y counts from J0).  With ready_hi >= 0 only the stars of the
-// particles in bin rows [ready_lo, ready_hi) (cyclically) are read: a pipelined call computes
-// the rest concurrently.
 template <typename P, typename V, typename R>
 __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs a, StarTab t,
-                                                                        NodeRecs r, int J0 = 0,
-                                                                        int J1 = 0x7fffffff,
-                                                                        int ready_lo = 0,
-                                                                        int ready_hi = -1)
+                                                                        NodeRecs r)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int J = J0 + blockIdx.y * 8 + (threadIdx.x >> 4);
-    if (I >= a.n || J >= a.n || J >= J1) return;
-    if (ready_hi >= 0) {
-        t.lo = __ldg(a.B.start + (long long)ready_lo * a.B.nb);
-        t.hi = __ldg(a.B.start + (long long)ready_hi * a.B.nb);
-    }
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
     geom_node<P, V, R>(a, t, r, I, J, (long long)J * a.n + I);
 }
 
@@ -705,12 +695,10 @@ template <typename S, int REFINE> constexpr int solve_min_blocks()
 }
 
 template <typename P, typename V, typename R, typename S, int REFINE>
-__global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solve(P2MArgs a, NodeRecs r,
-                                                                                long long n0 = 0,
-                                                                                long long n1 = -1)
+__global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solve(P2MArgs a, NodeRecs r)
 {
-    const long long node = n0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (node >= r.nodes || (n1 >= 0 && node >= n1)) return;
+    const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (node >= r.nodes) return;
     const int meta = r.meta[node];
     if (meta < 0) return;
     const int nu = meta & 31;

@@ -30,49 +30,6 @@ __global__ void __launch_bounds__(64) k_star_retry(Bins B, int R0, StarTab t, De
         star_retry_slot(B, R0, t, t.queue[i], st);
 }
 
-// The particles of bin rows [row0, row1): slots [start[row0 nb], start[row1 nb]).  Their queue
-// is the table's queue from the first of those slots, with its own counter qc.
-__global__ void __launch_bounds__(STAR_TPB) k_star_list_rows(Bins B, int R0, StarTab t,
-                                                             DevStatus *st, int row0, int row1,
-                                                             int *qc)
-{
-    __shared__ float2 sxy[STAR_KL * STAR_TPB];
-    __shared__ unsigned skey[STAR_KL * STAR_TPB];
-    __shared__ int ss[STAR_KL * STAR_TPB];
-    __shared__ unsigned char sord[STAR_KL * STAR_TPB];
-    __shared__ unsigned char sstk[STAR_KL * STAR_TPB];
-    const long long v0 = __ldg(B.start + (long long)row0 * B.nb);
-    const long long v1 = __ldg(B.start + (long long)row1 * B.nb);
-    StarTab tc = t;
-    tc.queue = t.queue + v0;
-    tc.qcount = qc;
-    const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sord + threadIdx.x,
-                     sstk + threadIdx.x, STAR_TPB};
-    for (long long v = v0 + blockIdx.x * (long long)STAR_TPB + threadIdx.x; v < v1;
-         v += (long long)gridDim.x * STAR_TPB)
-        star_list_slot(B, R0, tc, v, L, st);
-}
-
-__global__ void __launch_bounds__(64) k_star_retry_rows(Bins B, int R0, StarTab t, DevStatus *st,
-                                                        int row0, const int *qc)
-{
-    const int *q = t.queue + __ldg(B.start + (long long)row0 * B.nb);
-    const int n = *qc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        star_retry_slot(B, R0, t, q[i], st);
-}
-
-cudaError_t launch_star_rows(const Bins &B, int R0, int rmax_far, const StarTab &t, DevStatus *st,
-                             int row0, int row1, int *qc, cudaStream_t s)
-{
-    k_star_list_rows<<<num_sms() * 5, STAR_TPB, 0, s>>>(B, R0, t, st, row0, row1, qc);
-    Bins Bf = B;
-    Bf.rmax = std::max(B.rmax, rmax_far);
-    k_star_retry_rows<<<num_sms() * 2, 64, 0, s>>>(Bf, R0, t, st, row0, qc);
-    count_launch(2);
-    return cudaGetLastError();
-}
-
 size_t star_tab_bytes(long long N)
 {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };

@@ -24,16 +24,7 @@ struct StarTab {
     int *qcount;        // number of queued slots
     long long N;
     unsigned gen;       // stamp of this call's entries (1 .. 2^24 - 1)
-    // Slots whose stars are complete, [lo, hi) cyclically; hi < 0: all.  A pipelined call
-    // reads only these (the rest may still be being written by a concurrent kernel).
-    int lo = 0, hi = -1;
 };
-
-__device__ __forceinline__ bool tab_ready(const StarTab &t, int v)
-{
-    if (t.hi < 0) return true;
-    return t.lo <= t.hi ? (v >= t.lo && v < t.hi) : (v >= t.lo || v < t.hi);
-}
 
 // A count entry carries the stamp of the call that wrote it, so that an entry left by an
 // earlier call (or not yet written by this one) reads as "not available" (-1) instead of as a
@@ -58,7 +49,7 @@ struct TabStar {
 
 __device__ __forceinline__ TabStar tab_star(const StarTab &t, int v)
 {
-    return {t.nbr + (long long)v * KMAX, tab_ready(t, v) ? tab_count(t, v) : -1};
+    return {t.nbr + (long long)v * KMAX, tab_count(t, v)};
 }
 
 // Apex of the Delaunay triangle to the left of the directed edge u -> w: the neighbour that

@@ -462,29 +462,3 @@ def test_fused_and_split_fast_pass_agree(P, solve):
     code, _ = api.pfem_read_status(small)
     assert code == 0
     assert torch.equal(fused, split)
-
-
-@pytest.mark.parametrize("solve", ["f32ref", "f32ff", "f32", "f64"])
-def test_pipelined_p2m_equals_sequential(P, solve):
-    """A context's pipelined quadratic P2M (node rows in 8 chunks; star tables, geometry and
-    solves on three streams, each chunk's solve overlapping later chunks' work) runs the same
-    kernels with the same per-node arithmetic as the sequential stages: bit-identical meshes on
-    the benchmarked workload and on uniform random particles, no device error."""
-    sv = {"f32": P.PFEM_SOLVE_F32, "f32ref": P.PFEM_SOLVE_F32_REFINED,
-          "f32ff": P.PFEM_SOLVE_F32_REFINED_FF, "f64": P.PFEM_SOLVE_F64}[solve]
-    N = 512 * 512
-    cases = [(G.config_large().pos, G.config_large().vals, 1025),
-             (G.uniform01(G.SEED_BASE + 62, 2 * N).reshape(N, 2), None, 257)]
-    for pos, vals, n in cases:
-        if vals is None:
-            vals = G.taylor_green(pos)
-        outs = []
-        for chunks in (8, 1):
-            ctx = P.Context(pipeline_chunks=chunks)
-            proj = P.Projector(n, pos.shape[0], C=vals.shape[1], pos_dtype=torch.float32, ctx=ctx)
-            proj.build(torch.tensor(pos, dtype=torch.float32, device="cuda"))
-            m = proj.p2m(torch.tensor(vals, dtype=torch.float32, device="cuda"),
-                         shape=P.PFEM_SHAPE_QUADRATIC, solve=sv)
-            proj.check()
-            outs.append(m)
-        assert torch.equal(outs[0], outs[1]), (n, solve)
