@@ -137,6 +137,30 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b)
 
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
 
+// Exact FP32 -> FP64 widening by integer operations on the bit patterns (sign; exponent
+// rebiased by 1023 - 127 = 896; the 23 mantissa bits at the top of the 52).  FP32 subnormals
+// (below 1.2e-38) become zero.  On sm_103a the format conversion instructions share the
+// narrow FP64 pipe, while these run on the integer pipes.
+__device__ __forceinline__ double f64_of(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned sign = u & 0x80000000u;
+    const unsigned hi = e ? sign | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu) : sign;
+    const unsigned lo = e ? u << 29 : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 -> FP32 by truncating the mantissa (relative error below 2^-23), for finite values
+// below FP32's largest; magnitudes below FP32's normal range become zero.
+__device__ __forceinline__ float f32_trunc(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned u = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return e > 0 ? __uint_as_float(u) : 0.0f;
+}
+
 // Refinement of the FP32 moment solve: 0 = none, 1 = residual in FP64, 2 = residual in
 // float-float.
 enum { REFINE_NONE = 0, REFINE_F64 = 1, REFINE_FF = 2 };

@@ -356,7 +356,7 @@ __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R
         const S b[6] = {S(0), S(0), S(0), S(-0.5) * tx * tx, S(-0.5) * tx * ty, S(-0.5) * ty * ty};
         S y[6];
         M.solve(b, y);
-        if (REFINE == REFINE_FF) {
+        if constexpr (REFINE == REFINE_FF) {
             // r = b - sum_mu p_mu (p_mu . y) in float-float, with the monomials of the FP32
             // offsets formed exactly (the same system the FP64 residual refines)
             FF r[6];
@@ -382,25 +382,33 @@ __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R
 #pragma unroll
             for (int k = 0; k < 6; ++k) y[k] += dy[k];
         }
-        if (REFINE == REFINE_F64) {
-            double r[6];
+        if constexpr (REFINE == REFINE_F64) {
+            // r = b - sum_mu p_mu (p_mu . y) in FP64: t = p . y by nested products, and the
+            // monomial terms of r as X (X t), Y (X t), Y (Y t)
+            double r[6], yd[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) r[k] = (double)b[k];
+            for (int k = 0; k < 6; ++k) {
+                r[k] = f64_of(b[k]);
+                yd[k] = f64_of(y[k]);
+            }
             for (unsigned m = mask; m; m &= m - 1) {
                 const int i = __ffs(m) - 1;
                 S ox, oy;
                 offset(i, ox, oy);
-                const double X = (double)((ox - mx) * inv), Y = (double)((oy - my) * inv);
-                const double p[6] = {1.0, X, Y, X * X, X * Y, Y * Y};
-                double t = 0.0;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) t = fma(p[k], (double)y[k], t);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) r[k] = fma(-p[k], t, r[k]);
+                const double X = f64_of((ox - mx) * inv), Y = f64_of((oy - my) * inv);
+                const double t = fma(X, fma(X, yd[3], fma(Y, yd[4], yd[1])),
+                                     fma(Y, fma(Y, yd[5], yd[2]), yd[0]));
+                const double xt = X * t, yt = Y * t;
+                r[0] -= t;
+                r[1] -= xt;
+                r[2] -= yt;
+                r[3] = fma(-X, xt, r[3]);
+                r[4] = fma(-Y, xt, r[4]);
+                r[5] = fma(-Y, yt, r[5]);
             }
             S rs[6], dy[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) rs[k] = (S)r[k];
+            for (int k = 0; k < 6; ++k) rs[k] = f32_trunc(r[k]);
             M.solve(rs, dy);
 #pragma unroll
             for (int k = 0; k < 6; ++k) y[k] += dy[k];
