@@ -692,14 +692,19 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
 }
 
 // Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
-// system without spills (sweep 8, 10, 12: 8); the FP64 residual of the refined solve needs 4.
+// system without spills (sweep 8, 10, 12: 8).  The refined solves take 6 (80 registers, a few
+// bytes of spills): the FP64 residual keeps the narrow FP64 pipe busy only with many warps in
+// flight (4, 6, 8: 6; one to three persistent blocks per SM measured 1.1 to 2.4 times slower).
 // (FP64 solves keep the single fused kernel, whose larger occupancy measured faster.)
 #ifndef PFEM_SOLVE_MIN_BLOCKS
 #define PFEM_SOLVE_MIN_BLOCKS 8
 #endif
+#ifndef PFEM_SOLVE_REF_MIN_BLOCKS
+#define PFEM_SOLVE_REF_MIN_BLOCKS 6
+#endif
 template <typename S, int REFINE> constexpr int solve_min_blocks()
 {
-    return (sizeof(S) == 8 || REFINE != REFINE_NONE) ? 4 : PFEM_SOLVE_MIN_BLOCKS;
+    return sizeof(S) == 8 ? 4 : REFINE != REFINE_NONE ? PFEM_SOLVE_REF_MIN_BLOCKS : PFEM_SOLVE_MIN_BLOCKS;
 }
 
 template <typename P, typename V, typename R, typename S, int REFINE>

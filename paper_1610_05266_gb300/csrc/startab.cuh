@@ -285,9 +285,45 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     }
     if (sp < 3) return -1;
     // certify every triangle (v, w_j, w_j+1): counter-clockwise, circumcircle inside the region
-    // and within D of v (then no particle outside the list can lie inside it).  The circle
-    // through v, a, b has centre -(P, Q) / 2K and passes through v; its radius r must satisfy
-    // r + err <= every clearance measured from the centre and <= D / 2.
+    // and within D of v (then no particle outside the list can lie inside it).
+    if (fminf(fminf(g.cl_lo_x, g.cl_hi_x), fminf(g.cl_lo_y, g.cl_hi_y)) >= 0.9995f * D) {
+        // The region holds the disk of radius 0.9995 D about v.  A circle through v of radius
+        // r = |a| |b| |a - b| / (2 |a x b|) lies within 2r of v, so 4 r^2 <= 0.997 D^2, i.e.
+        // la lb |a - b|^2 <= 0.997 D^2 K^2, keeps it inside both.  Each FP32 offset carries
+        // at most one rounding (2^-24, none below 2^24 units).  With K > 1e-3 of its summed
+        // magnitudes, K^2 is within 4e-4 of its exact value, and a and b are then at least
+        // 7e-4 rad apart as seen from v, so |a - b|^2 is within 4e-4 as well: the true 2r stays
+        // below 0.9989 D, inside the region, and every particle within the circle has an FP32
+        // squared distance below D^2, i.e. is in the list.
+        const float iD2 = __frcp_rn(D2);
+        for (int j = 0; j < sp; ++j) {
+            const float2 a = L.xy[L.stk[j * S] * S];
+            const float2 b = L.xy[L.stk[(j + 1 == sp ? 0 : j + 1) * S] * S];
+            const float k1 = a.x * b.y, k2 = a.y * b.x;
+            const float K = k1 - k2;
+            if (!(K > 1e-3f * (fabsf(k1) + fabsf(k2)))) {
+                // a thin triangle at v: the same bound from the exact offsets (64-bit
+                // integers, products in FP64 within 1e-15)
+                const int2 ea = exact_of(L.stk[j * S]);
+                const int2 eb = exact_of(L.stk[(j + 1 == sp ? 0 : j + 1) * S]);
+                const long long Ke = (long long)ea.x * eb.y - (long long)ea.y * eb.x;
+                if (Ke <= 0) return -1;
+                const long long ex = (long long)ea.x - eb.x, ey = (long long)ea.y - eb.y;
+                const double lae = (double)((long long)ea.x * ea.x + (long long)ea.y * ea.y);
+                const double lbe = (double)((long long)eb.x * eb.x + (long long)eb.y * eb.y);
+                const double labe = ((double)(ex * ex) + (double)(ey * ey)) / ((double)D * (double)D);
+                const double Kd = (double)Ke;
+                if (lae * lbe * labe > 0.997 * Kd * Kd) return -1;
+                continue;
+            }
+            const float dx = a.x - b.x, dy = a.y - b.y;
+            const float la = fmaf(a.x, a.x, a.y * a.y), lb = fmaf(b.x, b.x, b.y * b.y);
+            const float lab = fmaf(dx, dx, dy * dy) * iD2;
+            if (la * lb * lab > 0.997f * K * K) return -1;
+        }
+    } else {
+    // The circle through v, a, b has centre -(P, Q) / 2K and passes through v; its radius r
+    // must satisfy r + err <= every clearance measured from the centre and <= D / 2.
     for (int j = 0; j < sp; ++j) {
         const float2 a = L.xy[L.stk[j * S] * S];
         const float2 b = L.xy[L.stk[(j + 1 == sp ? 0 : j + 1) * S] * S];
@@ -300,6 +336,7 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
                                        fminf(g.cl_hi_y - ccy, g.cl_lo_y + ccy)),
                                  0.49995f * D) - err;
         if (!(room > 0.f) || fmaf(ccx, ccx, ccy * ccy) > room * room * 0.9999f) return -1;
+    }
     }
     if (sp > B.kcap) return -PFEM_ERR_CAPACITY;
     for (int j = 0; j < sp; ++j) out(j, L.s[L.stk[j * S] * S]);
