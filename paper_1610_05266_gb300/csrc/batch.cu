@@ -200,10 +200,18 @@ __global__ void __launch_bounds__(BSTAR) k_star_list_batch(const BPlanDev *pl, P
     }
 }
 
-// The queued particles of the table, each with its problem's bins and the widest radius.
+// The queued particles of the table, each with its problem's bins and the widest radius: the
+// hull attempt for a short queue, then the region search for the stars still queued.
+template <bool HULL>
 __global__ void __launch_bounds__(64) k_star_retry_batch(const BPlanDev *pl, P2MArgs base, StarTab t)
 {
+    __shared__ float2 sxy[HULL ? STAR_KL_RETRY * 64 : 1];
+    __shared__ unsigned skey[HULL ? STAR_KL_RETRY * 64 : 1];
+    __shared__ int ss[HULL ? STAR_KL_RETRY * 64 : 1];
+    __shared__ unsigned char sord[HULL ? STAR_KL_RETRY * 64 : 1];
+    __shared__ unsigned char sstk[HULL ? STAR_KL_RETRY * 64 : 1];
     const int n = min(*t.qcount, (int)min(t.N, (long long)0x7fffffff));
+    if (HULL && !short_queue(n, t.N)) return;
     const BDesc *D = plan_desc(pl);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int v = t.queue[i];
@@ -212,7 +220,13 @@ __global__ void __launch_bounds__(64) k_star_retry_batch(const BPlanDev *pl, P2M
         P2MArgs a;
         problem_args(a, base, d);
         a.B.rmax = max(d.rmax, d.nb / 4 - 1);
-        star_retry_slot(a.B, a.R0, t, v, a.status);
+        if constexpr (HULL) {
+            const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x,
+                             sord + threadIdx.x, sstk + threadIdx.x, 64};
+            star_retry_hull_slot(a.B, a.R0, t, v, L, a.status);
+        } else {
+            star_retry_slot(a.B, a.R0, t, v, a.status);
+        }
     }
 }
 
@@ -418,11 +432,12 @@ static cudaError_t p2m_batch_t(const void *plan, const P2MArgs &base, int shape_
     const int TYs[BT_SHAPES] = {4, 8, 16};
     if (SHAPE == PFEM_SHAPE_QUADRATIC && w.table) {
         k_star_list_batch<<<num_sms() * 8, BSTAR, 0, s>>>(pl, base, w.tab);
-        k_star_retry_batch<<<num_sms() * 4, 64, 0, s>>>(pl, base, w.tab);
+        k_star_retry_batch<true><<<num_sms() * PFEM_RETRY_BLOCKS, 64, 0, s>>>(pl, base, w.tab);
+        k_star_retry_batch<false><<<num_sms() * 4, 64, 0, s>>>(pl, base, w.tab);
         k_p2m_batch_geom<P, V, R><<<blocks, 16 * TYs[shape_idx], 0, s>>>(pl, shape_idx, base, counter,
                                                                       w.tab, w.recs);
         k_p2m_solve<P, V, R, S, REF><<<(unsigned)((w.recs.nodes + 127) / 128), 128, 0, s>>>(base, w.recs);
-        count_launch(4);
+        count_launch(5);
     } else {
         k_p2m_batch<P, V, R, S, REF, SHAPE><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
             pl, shape_idx, base, counter);

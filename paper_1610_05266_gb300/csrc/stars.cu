@@ -22,7 +22,25 @@ __global__ void __launch_bounds__(STAR_TPB) k_star_list(Bins B, int R0, StarTab 
     star_list_slot(B, R0, t, v, L, st);
 }
 
-// The queued particles, with the radius of B (the launcher passes the widest one).
+// The queued particles, with the radius of B (the launcher passes the widest one): the hull
+// attempt for a short queue (lists in shared memory as in k_star_list, 32 x 18 bytes x 64
+// threads = 36 KB), then the region search for the stars still queued.
+constexpr int RETRY_TPB = 64;
+__global__ void __launch_bounds__(RETRY_TPB) k_star_retry_hull(Bins B, int R0, StarTab t, DevStatus *st)
+{
+    __shared__ float2 sxy[STAR_KL_RETRY * RETRY_TPB];
+    __shared__ unsigned skey[STAR_KL_RETRY * RETRY_TPB];
+    __shared__ int ss[STAR_KL_RETRY * RETRY_TPB];
+    __shared__ unsigned char sord[STAR_KL_RETRY * RETRY_TPB];
+    __shared__ unsigned char sstk[STAR_KL_RETRY * RETRY_TPB];
+    const HullList L{sxy + threadIdx.x, skey + threadIdx.x, ss + threadIdx.x, sord + threadIdx.x,
+                     sstk + threadIdx.x, RETRY_TPB};
+    const int n = min(*t.qcount, (int)min(t.N, (long long)0x7fffffff));
+    if (!short_queue(n, t.N)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        star_retry_hull_slot(B, R0, t, t.queue[i], L, st);
+}
+
 __global__ void __launch_bounds__(64) k_star_retry(Bins B, int R0, StarTab t, DevStatus *st)
 {
     const int n = min(*t.qcount, (int)min(t.N, (long long)0x7fffffff));
@@ -71,8 +89,9 @@ cudaError_t launch_star_table(const Bins &B, int R0, int rmax_far, const StarTab
     k_star_list<<<(unsigned)((t.N + STAR_TPB - 1) / STAR_TPB), STAR_TPB, 0, s>>>(B, R0, t, st);
     Bins Bf = B;
     Bf.rmax = std::max(B.rmax, rmax_far);
+    k_star_retry_hull<<<num_sms() * PFEM_RETRY_BLOCKS, RETRY_TPB, 0, s>>>(Bf, R0, t, st);
     k_star_retry<<<num_sms() * 4, 64, 0, s>>>(Bf, R0, t, st);
-    count_launch(2);
+    count_launch(3);
     return cudaGetLastError();
 }
 

@@ -113,15 +113,15 @@ __device__ __forceinline__ unsigned pack_key(float x, float y, int k)
     return ((unsigned)(a * 33554432.0f) << 5) | (unsigned)k;
 }
 
-// Sort 16 packed keys (bitonic network, unrolled: the array stays in registers).
-__device__ __forceinline__ void sort16(unsigned (&w)[16])
+// Sort KLC packed keys (bitonic network, unrolled: the array stays in registers).
+template <int KLC> __device__ __forceinline__ void sort_keys(unsigned (&w)[KLC])
 {
 #pragma unroll
-    for (int size = 2; size <= 16; size <<= 1)
+    for (int size = 2; size <= KLC; size <<= 1)
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1)
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < KLC; ++i) {
                 const int j = i ^ stride;
                 if (j > i) {
                     const unsigned a = w[i], b = w[j];
@@ -133,7 +133,7 @@ __device__ __forceinline__ void sort16(unsigned (&w)[16])
             }
 }
 
-// The Delaunay star of v from the candidates within distance D (at most 16), by the convex
+// The Delaunay star of v from the candidates within distance D (at most KLC, 16 or 32), by the convex
 // hull of the candidates inverted about v.  Inversion c -> c/|c|^2 maps the circles through v
 // to lines, so an empty circle through v, a, b becomes a hull edge between the images of a
 // and b; and the orientation of three images is the sign of the lifted incircle determinant of
@@ -143,11 +143,11 @@ __device__ __forceinline__ void sort16(unsigned (&w)[16])
 // scan starting at u0, then certify every triangle (v, w_j, w_j+1) as the gift-wrapping search
 // does (the circumcircle inside the searched region and within D of v).  Returns the count,
 // -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
-template <typename Out>
+template <int KLC, typename Out>
 __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const Region &g, float D,
                                          const HullList &L, Out &&out)
 {
-    constexpr int KLC = 16;
+    static_assert(KLC == 16 || KLC == 32, "the packed key holds a 5-bit list index");
     const int S = L.stride;
     int cnt = 0, u0 = -1, s0 = 0x7fffffff;
     long long d2b = 0x7fffffffffffffffLL;
@@ -191,14 +191,14 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     // than KEY_NEAR (near-equal angles by the exact cross product; on one ray the farther
     // particle first: its image lies inside the hull and the scan removes it, and on u0's ray
     // this puts the farther particles just before u0, i.e. at the end of the scan from u0).
-    unsigned w[16];
+    unsigned w[KLC];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = k < cnt ? L.pk[k * S] : 0xffffffffu;
-    sort16(w);
+    for (int k = 0; k < KLC; ++k) w[k] = k < cnt ? L.pk[k * S] : 0xffffffffu;
+    sort_keys<KLC>(w);
     bool near = false;
     int p0 = 0;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < KLC; ++k) {
         if (k < cnt) L.ord[k * S] = (unsigned char)(w[k] & 31u);
         if (k + 1 < cnt && (w[k + 1] >> 5) - (w[k] >> 5) < KEY_NEAR) near = true;
         if (k < cnt && (int)(w[k] & 31u) == u0) p0 = k;
@@ -351,7 +351,7 @@ __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const Star
     int *out = t.nbr + v * KMAX;
     int c = -1;
     if (B.dmax > 0.f)
-        c = star_hull(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
+        c = star_hull<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
                                [&](int k, int s) { out[k] = s; });
     if (c == -1) {
         t.cnt[v] = tab_pack(t.gen, -1);
@@ -362,11 +362,34 @@ __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const Star
     if (c < 0) record_error(st, -c, v);
 }
 
-// A queued slot: the wide list attempt and then growing regions (star_region) up to B.rmax.  A
-// star that still fails records its error (an exhausted region as PFEM_ERR_CAPACITY).
+// A queued slot, first pass (short queues only): the hull attempt again over a 32-entry list at
+// 1.25 times the cutoff (a circumcircle a little wider than the first cutoff: at jitter 0.25 the
+// Delaunay circumdiameter of a jittered lattice can reach 2.12 spacings).  A star it cannot
+// certify keeps its queued mark for star_retry_slot.
+constexpr int STAR_KL_RETRY = 32;
+__device__ __forceinline__ void star_retry_hull_slot(const Bins &B, int R0, const StarTab &t, int v,
+                                                     const HullList &L, DevStatus *st)
+{
+    if (!(B.dmax > 0.f)) return;
+    const uint2 pv = __ldg(B.q + v);
+    int *out = t.nbr + (long long)v * KMAX;
+    const float D = 1.25f * B.dmax;
+    const int R = max(R0, (int)ceilf(D * (float)B.nb * 2.3283064365386963e-10f));
+    if (R > B.rmax) return;
+    const int c = star_hull<STAR_KL_RETRY>(B, v, pv, make_region(B, pv, R), D, L,
+                                           [&](int k, int s) { out[k] = s; });
+    if (c == -1) return;
+    t.cnt[v] = tab_pack(t.gen, c);
+    if (c < 0) record_error(st, -c, v);
+}
+
+// A queued slot still marked queued: the wide list attempt and then growing regions
+// (star_region) up to B.rmax.  A star that still fails records its error (an exhausted region
+// as PFEM_ERR_CAPACITY).
 __device__ __forceinline__ void star_retry_slot(const Bins &B, int R0, const StarTab &t, int v,
                                                 DevStatus *st)
 {
+    if (tab_count(t, v) != -1) return;
     int loc[KMAX];
     int c = star_region(B, v, __ldg(B.q + v), R0, loc);
     if (c > 0) {
@@ -378,5 +401,14 @@ __device__ __forceinline__ void star_retry_slot(const Bins &B, int R0, const Sta
     }
     t.cnt[v] = tab_pack(t.gen, c);
 }
+
+// Blocks per SM of the hull retry kernels (64 threads and 36 KB of lists each).
+#ifndef PFEM_RETRY_BLOCKS
+#define PFEM_RETRY_BLOCKS 6
+#endif
+// The hull retry runs for queues up to 1/64 of the particles: on irregular particle sets
+// (uniform random: 56 % of the stars queued) a quarter of the queued stars fail it too, and the
+// wide attempt alone measured faster.
+__device__ __forceinline__ bool short_queue(int n, long long N) { return n <= (N >> 6); }
 
 }  // namespace pfem
