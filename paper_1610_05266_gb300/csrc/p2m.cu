@@ -116,7 +116,10 @@ static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
     if (e != cudaSuccess || a.defer_cap <= 0) return e;
     P2MArgs f = a;
     f.B.rmax = rmax_far > a.B.rmax ? rmax_far : a.B.rmax;
-    k_p2m_fix<P, V, R, SHAPE, W><<<num_sms(), 128, 0, s>>>(f);
+    if (SHAPE == PFEM_SHAPE_QUADRATIC && !W && rec && tab)
+        k_p2m_fix_tab<P, V, R, sizeof(S) == 4><<<num_sms(), 128, 0, s>>>(f, *tab);
+    else
+        k_p2m_fix<P, V, R, SHAPE, W><<<num_sms(), 128, 0, s>>>(f);
     count_launch();
     stage_event(g, 4, s);
     return cudaGetLastError();

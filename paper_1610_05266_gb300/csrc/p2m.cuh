@@ -691,6 +691,64 @@ __global__ void __launch_bounds__(128, PFEM_GEOM_MIN_BLOCKS) k_p2m_geom(P2MArgs 
     geom_node<P, V, R>(a, t, r, I, J, (long long)J * a.n + I);
 }
 
+// The fix pass of the table path: the queued nodes located with the star table (complete after
+// the retry kernels; the launcher passes the widest search radius for the nearest particle) and
+// every edge solved in FP64 by the SVD, as k_p2m_fix does with stars searched per thread.  With
+// CHOL (runs whose fast pass solved in FP32) a node first takes the FP64 Cholesky solve of the
+// FP64 fast path, pivot tolerance included: a system too ill-conditioned for the FP32 solve is
+// usually well within FP64's, and only the nodes below that tolerance (rank deficient, or
+// conditioned beyond it) take the SVD.
+template <typename P, typename V, typename R, bool CHOL>
+__global__ void __launch_bounds__(128) k_p2m_fix_tab(P2MArgs a, StarTab t)
+{
+    const int cnt = min(*a.defer_count, a.defer_cap);
+    P2MArgs f = a;
+    f.defer_cap = 0;
+    const int nc = a.n - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const long long node = a.defer_list[i];
+        const int I = (int)(node % a.n), J = (int)(node / a.n);
+        const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+        const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+        int tri[3];
+        int st = locate_tab(f.B, t, qn, f.R0, tri);
+        if (st == -PFEM_FAR) st = -PFEM_ERR_CAPACITY;
+        TabStar sa[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            if (st == 0) {
+                sa[e] = tab_star(t, tri[e]);
+                if (sa[e].n < 0) st = sa[e].n == -1 ? -PFEM_ERR_CAPACITY : sa[e].n;
+            }
+        NodePos<P, R> np;
+        np.init(Iu, Ju, nc);
+        R acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = R(0);
+        if (st == 0) {
+            R lam[3];
+            barycentric(f, np, tri, lam);
+            auto emit = [&](int sl, R wgt) {
+                R v[8];
+                load_vals<V, R>((const V *)f.vals, f.perm, sl, f.C, v);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < f.C) acc[c] = fma(wgt, v[c], acc[c]);
+            };
+            st = CHOL ? node_quadratic<P, R, double, REFINE_NONE, false>(f, np, tri, sa, lam, emit)
+                      : -PFEM_DEFER;
+            if (st == -PFEM_DEFER)      // nothing was emitted
+                st = node_quadratic<P, R, double, REFINE_NONE, true>(f, np, tri, sa, lam, emit);
+        }
+        if (st != 0) {
+            record_error(f.status, -st, node);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+        }
+        store_vals<V, R>((V *)f.out, node, f.C, acc);
+    }
+}
+
 // Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
 // system without spills (sweep 8, 10, 12: 8).  The refined solves take 6 (80 registers, a few
 // bytes of spills): the FP64 residual keeps the narrow FP64 pipe busy only with many warps in
