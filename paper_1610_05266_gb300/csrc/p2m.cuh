@@ -220,8 +220,7 @@ __device__ __forceinline__ void store_vals<float, float>(float *out, long long n
         if (c < C) out[node * C + c] = acc[c];
 }
 
-// A star as a list of slots: plain slot array (per-thread path) or shared-memory indices
-// mapped to slots (tiled path).
+// A star as a plain array of slots (the stars a thread searched itself).
 struct ArrStar {
     const int *p;
     int n;

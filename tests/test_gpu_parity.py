@@ -263,25 +263,6 @@ def test_reduced_precision_errors_tiny(P):
         assert e < (1e-5 if "float32" in vt else 2e-2)
 
 
-@pytest.mark.parametrize("dtype,shape", [(torch.float64, 1), (torch.float32, 1), (torch.float64, 0)])
-def test_tiled_and_per_thread_paths_agree(P, dtype, shape, monkeypatch):
-    """The shared-memory tiled P2M and the per-thread global-memory P2M compute the same
-    topology and the same arithmetic: outputs are bit-identical (mesh sizes chosen so that
-    tiles of 16, 8 and 4 nodes and the per-thread-only case all occur)."""
-    for n, M in ((33, 64), (129, 256), (100, 396), (65, 256)):
-        pos = G.jittered_lattice(M, 0.25, G.SEED_BASE + n)
-        vals = G.taylor_green(pos, k=3)
-        pr = G.Problem("t", n, M, 0.25, 0, pos, vals)
-        proj, _ = gpu_setup(P, pr, dtype)
-        v = torch.tensor(vals, dtype=dtype, device="cuda")
-        monkeypatch.setenv("PFEM_TILED", "1")
-        tiled = proj.p2m(v, shape=shape)
-        monkeypatch.delenv("PFEM_TILED")
-        plain = proj.p2m(v, shape=shape)
-        proj.check()
-        assert torch.equal(tiled, plain), (n, M)
-
-
 def test_m2p_mesh_qcsf_matches_oracle(P):
     """M2P with quadratically consistent mesh shape functions (the paper's projFEM6/projFEMq
     interpolation): FP64 within 1e-12 of the oracle on ragged sizes; reduced-precision errors
