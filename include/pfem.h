@@ -132,6 +132,14 @@ const char *pfem_last_error(const pfem_ctx *ctx);
  * with cudaEventElapsedTime after synchronising.  Recording adds no work to the kernels. */
 pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count);
 
+/* An event (cudaEvent_t as void*) that pfem_project_p2m calls made with this context wait on
+ * (cudaStreamWaitEvent on the call's stream) right before their first kernel that reads the
+ * particle values -- after the star table and the node records of the quadratic path, at the
+ * start of the others; NULL (the default) clears it.  A caller can so copy the values on another
+ * stream while the call works on the positions.  The event must have been recorded (or never
+ * recorded: then the wait is a no-op) when the call is made. */
+pfem_status pfem_set_values_event(pfem_ctx *ctx, void *event);
+
 /* Version of this ABI. */
 int pfem_abi_version(void);
 

@@ -37,6 +37,7 @@ SIGNATURES = {
     "pfem_get_options": (ctypes.c_int, [_p, _p]),
     "pfem_last_error": (ctypes.c_char_p, [_p]),
     "pfem_set_stage_events": (ctypes.c_int, [_p, _p, _i32]),
+    "pfem_set_values_event": (ctypes.c_int, [_p, _p]),
     "pfem_default_bins": (_i32, [_i32, _i64]),
     "pfem_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
     "pfem_read_status": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _p]),

@@ -59,6 +59,15 @@ class Context:
               "pfem_set_stage_events", self)
         self._events = list(events)
 
+    def set_values_event(self, event):
+        """A torch.cuda.Event that later P2M calls wait on before their first kernel that reads
+        the particle values (pfem_set_values_event); None clears it."""
+        if event is not None and not event.cuda_event:
+            event.record()
+        h = ctypes.c_void_p(event.cuda_event) if event is not None else None
+        check(self._lib.pfem_set_values_event(self.handle, h), "pfem_set_values_event", self)
+        self._values_event = event
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:
@@ -425,6 +434,74 @@ def projection_loop(proj: Projector, pos: torch.Tensor, mesh: torch.Tensor,
             proj.build(pos, stream=stream)
         mesh = proj.p2m(vals, shape=p2m_shape, solve=solve, stream=stream)
     return pos, mesh
+
+
+class HostRoundTrip:
+    """The round trip from host memory, step after step: the positions and values of a step are
+    copied from pinned host buffers, binned, projected onto the mesh (P2M) and back onto the
+    particles (M2P), and the particle values are copied back into a pinned host buffer.
+
+    The copies overlap the compute: a step's inputs go on their own stream into one of two device
+    buffer sets while the previous step computes; P2M waits for the values only before its first
+    kernel that reads them (the context's values event, pfem_set_values_event); the result goes
+    back on a third stream while the next step runs.  step() returns at once; wait() blocks until
+    the last step's result is in its host buffer.  proj must have a context (one is created if
+    it has none)."""
+
+    def __init__(self, proj: "Projector", C: int, dtype=torch.float32, shape=PFEM_SHAPE_QUADRATIC,
+                 solve=None, m2p_shape=PFEM_SHAPE_LINEAR, stream=None):
+        if proj.ctx is None:
+            proj.ctx = Context()
+        self.proj, self.shape, self.solve, self.m2p_shape = proj, shape, solve, m2p_shape
+        dev = proj.device
+        pos_t = proj.cells.pos_sorted.dtype
+        self.pos_d = [torch.empty((proj.N, 2), dtype=pos_t, device=dev) for _ in range(2)]
+        self.vals_d = [torch.empty((proj.N, C), dtype=dtype, device=dev) for _ in range(2)]
+        self.mesh = torch.empty((proj.n, proj.n, C), dtype=dtype, device=dev)
+        self.back = torch.empty((proj.N, C), dtype=dtype, device=dev)
+        self.stream = stream or torch.cuda.current_stream(dev)
+        self.h2d = torch.cuda.Stream(dev)
+        self.d2h = torch.cuda.Stream(dev)
+        ev = lambda: torch.cuda.Event()
+        self.ev_pos, self.ev_vals, self.ev_free = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        self.ev_done, self.ev_out = ev(), ev()
+        self.k = 0
+
+    def step(self, pos_h: torch.Tensor, vals_h: torch.Tensor, out_h: torch.Tensor):
+        b = self.k & 1
+        s, h2d, d2h = self.stream, self.h2d, self.d2h
+        with torch.cuda.stream(h2d):
+            if self.k >= 2:
+                h2d.wait_event(self.ev_free[b])       # step k-2 is done with buffer set b
+            self.pos_d[b].copy_(pos_h, non_blocking=True)
+            self.ev_pos[b].record(h2d)
+            self.vals_d[b].copy_(vals_h, non_blocking=True)
+            self.ev_vals[b].record(h2d)
+        s.wait_event(self.ev_pos[b])
+        proj = self.proj
+        proj.build(self.pos_d[b], stream=s)
+        proj.ctx.set_values_event(self.ev_vals[b])
+        try:
+            proj.p2m(self.vals_d[b], shape=self.shape, solve=self.solve, out=self.mesh, stream=s)
+        finally:
+            proj.ctx.set_values_event(None)
+        if self.k >= 1:
+            s.wait_event(self.ev_out)                 # the previous result has left self.back
+        proj.m2p(self.pos_d[b], self.mesh, out=self.back, shape=self.m2p_shape, stream=s)
+        self.ev_free[b].record(s)
+        self.ev_done.record(s)
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(self.ev_done)
+            out_h.copy_(self.back, non_blocking=True)
+            self.ev_out.record(d2h)
+        self.k += 1
+
+    def wait(self):
+        self.ev_out.synchronize()
+
+    def join(self, stream=None):
+        """Make `stream` (default: the compute stream) wait for the last result's copy."""
+        (stream or self.stream).wait_event(self.ev_out)
 
 
 class Batch:

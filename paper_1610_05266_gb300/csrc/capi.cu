@@ -72,6 +72,7 @@ struct pfem_ctx {
     char err[512];
     void *events[8];            // stage events (cudaEvent_t) recorded by pfem_project_p2m
     int nevents;
+    void *vals_event;           // event pfem_project_p2m waits on before reading the values
 };
 
 static thread_local char t_err[512];
@@ -199,6 +200,7 @@ static pfem_status make_geo(const pfem_ctx *ctx, const char *fn, int32_t n, int3
     g->ucap = o.node_capacity;
     g->events = ctx && ctx->nevents > 0 ? ctx->events : nullptr;
     g->nevents = ctx ? ctx->nevents : 0;
+    g->vals_event = ctx ? ctx->vals_event : nullptr;
     return PFEM_OK;
 }
 
@@ -245,6 +247,7 @@ pfem_status pfem_create(pfem_ctx **ctx, const pfem_options *opt)
     c->opt = o;
     c->err[0] = 0;
     c->nevents = 0;
+    c->vals_event = nullptr;
     *ctx = c;
     return ok(nullptr);
 }
@@ -259,6 +262,13 @@ pfem_status pfem_get_options(const pfem_ctx *ctx, pfem_options *opt)
 }
 
 const char *pfem_last_error(const pfem_ctx *ctx) { return err_buf(ctx); }
+
+pfem_status pfem_set_values_event(pfem_ctx *ctx, void *event)
+{
+    if (!ctx) return say(nullptr, PFEM_ERR_INVALID_ARG, "pfem_set_values_event: needs a context");
+    ctx->vals_event = event;
+    return ok(ctx);
+}
 
 pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count)
 {
@@ -402,7 +412,9 @@ pfem_status pfem_project_p2m(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N,
             return say(ctx, PFEM_ERR_INVALID_ARG, "%s: explicit weights need w_idx, w and K in 3..PFEM_KW_MAX", fn);
         if (!((val_t == PFEM_F64 && w_t == PFEM_F64) || (val_t != PFEM_F64 && w_t == PFEM_F32)))
             return say(ctx, PFEM_ERR_INVALID_ARG, "%s: weights dtype does not match the values", fn);
-        return cuda_result(ctx, launch_apply(n, perm, C, vals, val_t, w_idx, w, K, w_t, mesh_vals, s), fn);
+        cudaError_t e = wait_values(g, s);
+        if (e == cudaSuccess) e = launch_apply(n, perm, C, vals, val_t, w_idx, w, K, w_t, mesh_vals, s);
+        return cuda_result(ctx, e, fn);
     }
     if (!shape_ok(shape) || !solve_ok(solve)) return say(ctx, PFEM_ERR_INVALID_ARG, "%s: unknown shape or solve", fn);
     // FP64 values use FP64 positions and the FP64 solve; FP32/BF16 values use FP32 positions

@@ -64,7 +64,14 @@ struct GeoArgs {
     int ucap;                   // distinct particles of one node in the fast pass (<= PFEM_UMAX)
     void *const *events = nullptr;  // stage events of the caller's context (cudaEvent_t), or null
     int nevents = 0;
+    void *vals_event = nullptr;     // the context's values event (cudaEvent_t), or null
 };
+
+// Make stream s wait for the context's values event before a kernel that reads the values.
+inline cudaError_t wait_values(const GeoArgs &g, cudaStream_t s)
+{
+    return g.vals_event ? cudaStreamWaitEvent(s, (cudaEvent_t)g.vals_event, 0) : cudaSuccess;
+}
 
 // Record stage event k of g on stream s (no-op without events).
 inline void stage_event(const GeoArgs &g, int k, cudaStream_t s)

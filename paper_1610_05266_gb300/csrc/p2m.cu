@@ -106,11 +106,19 @@ static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         stage_event(g, 2, s);
+        if (!W) {
+            e = wait_values(g, s);
+            if (e != cudaSuccess) return e;
+        }
         k_p2m_solve<P, V, R, S, REF><<<(unsigned)((rec->nodes + 127) / 128), 128, 0, s>>>(a, *rec);
         count_launch();
         e = cudaGetLastError();
         stage_event(g, 3, s);
     } else {
+        if (!W) {
+            e = wait_values(g, s);
+            if (e != cudaSuccess) return e;
+        }
         e = go_fast<P, V, R, S, REF, SHAPE, W>(a, s);
     }
     if (e != cudaSuccess || a.defer_cap <= 0) return e;

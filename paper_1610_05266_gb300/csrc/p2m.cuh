@@ -620,9 +620,11 @@ inline size_t node_recs_layout(char *base, long long nodes, NodeRecs *r, bool wi
     return total;
 }
 
-// Resident 128-thread blocks per SM of the geometry kernel.
+// Resident 128-thread blocks per SM of the geometry kernel: its node search waits on memory,
+// and more warps in flight hide it (8, 10, 12, 16 blocks measured 0.291, 0.275, 0.268, 0.266 ms
+// at 1025^2 nodes / 2048^2 particles); 12 keeps the register spills to a few dozen bytes.
 #ifndef PFEM_GEOM_MIN_BLOCKS
-#define PFEM_GEOM_MIN_BLOCKS 8
+#define PFEM_GEOM_MIN_BLOCKS 12
 #endif
 // Node (I, J) of the mesh of a.n nodes per side: locate it and build its particle set from the
 // star table, and write its record at index `rec` (node J * a.n + I of a single problem; the

@@ -130,3 +130,32 @@ def test_zalesak_loop_matches_oracle(P, m2p_shape, p2m_shape):
         err = np.abs(mesh.cpu().numpy() - ref_mesh).max() / np.abs(ref_mesh).max()
         assert err <= 1e-12, err
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_host_round_trip_matches_device_steps(P):
+    """HostRoundTrip (input copies on their own stream into two alternating buffer sets, P2M
+    waiting on the values event before its first kernel that reads the values, results copied
+    back on a third stream) returns, step after step, the particle values of build -> P2M -> M2P
+    on device-resident inputs, bit for bit; two input sets alternate so that every buffer
+    hand-over is exercised."""
+    n, M, C = 129, 256, 3
+    sets = []
+    for k in range(2):
+        pos = G.jittered_lattice(M, 0.25, G.SEED_BASE + 520 + k).astype(np.float32)
+        vals = G.taylor_green(pos.astype(np.float64), k=2 + k).astype(np.float32)
+        sets.append((torch.tensor(pos).pin_memory(), torch.tensor(vals).pin_memory()))
+    proj = P.Projector(n, M * M, C=C, pos_dtype=torch.float32, ctx=P.Context())
+    ref = []
+    for pos_h, vals_h in sets:
+        pos_d, vals_d = pos_h.cuda(), vals_h.cuda()
+        proj.build(pos_d)
+        mesh = proj.p2m(vals_d, solve=P.PFEM_SOLVE_F32_REFINED)
+        ref.append(proj.m2p(pos_d, mesh).cpu())
+    rt = P.HostRoundTrip(proj, C, solve=P.PFEM_SOLVE_F32_REFINED)
+    outs = [torch.empty((M * M, C), dtype=torch.float32).pin_memory() for _ in range(6)]
+    for k, out_h in enumerate(outs):
+        rt.step(*sets[k % 2], out_h)
+    rt.wait()
+    proj.check()
+    for k, out_h in enumerate(outs):
+        assert torch.equal(out_h, ref[k % 2]), k
