@@ -659,7 +659,10 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const StarTab &t, co
         if (node_u_sets<UMAX>(tri, sa, us, nu, vm, vi, min(a.ucap, UMAX)) != 0) {
             st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
         } else {
-            for (int i = 0; i < nu; ++i) r.us[i * r.nodes + rec] = us[i];
+            // entries up to the warp's largest set, -1 past this node's: the warp writes whole
+            // sectors of each entry array (a partly written sector costs a read to complete)
+            const int nw = __reduce_max_sync(__activemask(), nu);
+            for (int i = 0; i < nw; ++i) r.us[i * r.nodes + rec] = i < nu ? us[i] : -1;
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 r.mask[e * r.nodes + rec] = vm[e];

@@ -143,9 +143,9 @@ template <int KLC> __device__ __forceinline__ void sort_keys(unsigned (&w)[KLC])
 // scan starting at u0, then certify every triangle (v, w_j, w_j+1) as the gift-wrapping search
 // does (the circumcircle inside the searched region and within D of v).  Returns the count,
 // -1 (list overflow or not certified: the caller retries wider) or -PFEM_ERR_*.
-template <int KLC, typename Out>
+template <int KLC>
 __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const Region &g, float D,
-                                         const HullList &L, Out &&out)
+                                         const HullList &L, int *row)
 {
     static_assert(KLC == 16 || KLC == 32, "the packed key holds a 5-bit list index");
     const int S = L.stride;
@@ -339,7 +339,18 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     }
     }
     if (sp > B.kcap) return -PFEM_ERR_CAPACITY;
-    for (int j = 0; j < sp; ++j) out(j, L.s[L.stk[j * S] * S]);
+    // the row (64-byte aligned) in whole 32-byte sectors by 16-byte stores, -1 after the star:
+    // a partly written sector would cost the memory system a read to complete it
+    const int nq = ((sp + 7) >> 3) << 1;
+    for (int q = 0; q < nq; ++q) {
+        int e[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            e[i] = -1;
+            if (4 * q + i < sp) e[i] = L.s[L.stk[(4 * q + i) * S] * S];
+        }
+        reinterpret_cast<int4 *>(row)[q] = make_int4(e[0], e[1], e[2], e[3]);
+    }
     return sp;
 }
 
@@ -351,8 +362,7 @@ __device__ __forceinline__ void star_list_slot(const Bins &B, int R0, const Star
     int *out = t.nbr + v * KMAX;
     int c = -1;
     if (B.dmax > 0.f)
-        c = star_hull<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L,
-                               [&](int k, int s) { out[k] = s; });
+        c = star_hull<STAR_KL>(B, (int)v, pv, make_region(B, pv, R0), B.dmax, L, out);
     if (c == -1) {
         t.cnt[v] = tab_pack(t.gen, -1);
         t.queue[atomicAdd(t.qcount, 1)] = (int)v;   // at most N entries: each slot once
@@ -376,8 +386,7 @@ __device__ __forceinline__ void star_retry_hull_slot(const Bins &B, int R0, cons
     const float D = 1.25f * B.dmax;
     const int R = max(R0, (int)ceilf(D * (float)B.nb * 2.3283064365386963e-10f));
     if (R > B.rmax) return;
-    const int c = star_hull<STAR_KL_RETRY>(B, v, pv, make_region(B, pv, R), D, L,
-                                           [&](int k, int s) { out[k] = s; });
+    const int c = star_hull<STAR_KL_RETRY>(B, v, pv, make_region(B, pv, R), D, L, out);
     if (c == -1) return;
     t.cnt[v] = tab_pack(t.gen, c);
     if (c < 0) record_error(st, -c, v);
@@ -394,7 +403,7 @@ __device__ __forceinline__ void star_retry_slot(const Bins &B, int R0, const Sta
     int c = star_region(B, v, __ldg(B.q + v), R0, loc);
     if (c > 0) {
         int *out = t.nbr + (long long)v * KMAX;
-        for (int k = 0; k < c; ++k) out[k] = loc[k];
+        for (int k = 0; k < ((c + 7) & ~7); ++k) out[k] = k < c ? loc[k] : -1;
     } else {
         if (c == -PFEM_FAR || c == -1) c = -PFEM_ERR_CAPACITY;
         record_error(st, -c, v);
