@@ -659,8 +659,8 @@ __device__ __forceinline__ void geom_node(const P2MArgs &a, const StarTab &t, co
         if (node_u_sets<UMAX>(tri, sa, us, nu, vm, vi, min(a.ucap, UMAX)) != 0) {
             st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
         } else {
-            // entries up to the warp's largest set, -1 past this node's: the warp writes whole
-            // sectors of each entry array (a partly written sector costs a read to complete)
+            // entries up to the warp's largest set, -1 past this node's, so that the warp's
+            // stores to each entry array cover contiguous runs of it
             const int nw = __reduce_max_sync(__activemask(), nu);
             for (int i = 0; i < nw; ++i) r.us[i * r.nodes + rec] = i < nu ? us[i] : -1;
 #pragma unroll
