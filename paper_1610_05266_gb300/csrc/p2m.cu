@@ -47,6 +47,14 @@ static P2MArgs make_args(const GeoArgs &g, DevStatus *st)
 
 static dim3 node_grid(int n) { return dim3((n + 15) / 16, (n + 7) / 8); }
 
+// The table path's fast pass as one kernel (k_p2m_tab) or as the geometry and solve kernels with
+// node records in between.  Measured at 1025^2 nodes / 2048^2 particles (geometry + solve):
+// FP64-residual refinement 1.21 -> 1.07 ms fused, plain FP32 0.58 -> 0.53 ms, float-float
+// refinement 0.84 -> 0.89 ms; the float-float solve keeps the two kernels.
+#ifndef PFEM_P2M_FUSED_TAB
+#define PFEM_P2M_FUSED_TAB 1
+#endif
+
 template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
 static cudaError_t go_fast(const P2MArgs &a, cudaStream_t s)
 {
@@ -101,6 +109,18 @@ static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
         e = launch_star_table(a.B, R0, rmax_far, *tab, a.status, s);
         if (e != cudaSuccess) return e;
         stage_event(g, 1, s);
+#if PFEM_P2M_FUSED_TAB
+        if (!W && REF != REFINE_FF) {
+            stage_event(g, 2, s);
+            e = wait_values(g, s);
+            if (e != cudaSuccess) return e;
+            k_p2m_tab<P, V, R, S, REF><<<node_grid(a.n), 128, 0, s>>>(a, *tab);
+            count_launch();
+            e = cudaGetLastError();
+            stage_event(g, 3, s);
+        } else
+#endif
+        {
         k_p2m_geom<P, V, R><<<node_grid(a.n), 128, 0, s>>>(a, *tab, *rec);
         count_launch();
         e = cudaGetLastError();
@@ -114,6 +134,7 @@ static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
         count_launch();
         e = cudaGetLastError();
         stage_event(g, 3, s);
+        }
     } else {
         if (!W) {
             e = wait_values(g, s);

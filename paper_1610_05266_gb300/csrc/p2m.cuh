@@ -822,4 +822,66 @@ __global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solv
     store_vals<V, R>((V *)a.out, node, a.C, acc);
 }
 
+// The table path's fast pass in one kernel: each thread locates its node with the star table,
+// builds its particle set and solves its three edge systems, without a node record in between.
+// The refined solve is bound by the FP64 pipe, which leaves the other pipes and the memory
+// system to the location work of the other warps.
+template <typename P, typename V, typename R, typename S, int REFINE>
+__global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_tab(P2MArgs a, StarTab t)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
+    const int nc = a.n - 1;
+    const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
+    const long long node = (long long)J * a.n + I;
+    const uint2 qn = make_uint2(node_fx(Iu, nc), node_fx(Ju, nc));
+    int tri[3];
+    int st = locate_tab(a.B, t, qn, a.R0, tri);
+    TabStar sa[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+        if (st == 0) {
+            sa[e] = tab_star(t, tri[e]);
+            if (sa[e].n < 0) st = sa[e].n == -1 ? -PFEM_FAR : sa[e].n;
+        }
+    R acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = R(0);
+    if (st == 0) {
+        NodePos<P, R> np;
+        np.init(Iu, Ju, nc);
+        R lam[3];
+        barycentric(a, np, tri, lam);
+        int us[UMAX];
+        int nu;
+        unsigned vm[3];
+        int vi[3];
+        if (node_u_sets<UMAX>(tri, sa, us, nu, vm, vi, min(a.ucap, UMAX)) != 0) {
+            st = a.defer_cap > 0 ? -PFEM_DEFER : -PFEM_ERR_CAPACITY;
+        } else {
+            R uw[UMAX];
+            for (int i = 0; i < nu; ++i) uw[i] = R(0);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) uw[vi[e]] += lam[e];
+            st = node_u_solve<P, R, S, REFINE, false, UMAX>(a, np, us, uw, vm, vi, lam);
+            if (st == 0)
+                for (int i = 0; i < nu; ++i) {
+                    R v[8];
+                    load_vals<V, R>((const V *)a.vals, a.perm, us[i], a.C, v);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < a.C) acc[c] = fma(uw[i], v[c], acc[c]);
+                }
+        }
+    }
+    if (st != 0) {
+        st = defer_or_error(a, st, node);
+        if (st < 0) record_error(a.status, -st, node);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
+    }
+    store_vals<V, R>((V *)a.out, node, a.C, acc);
+}
+
 }  // namespace pfem
