@@ -826,8 +826,18 @@ __global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solv
 // builds its particle set and solves its three edge systems, without a node record in between.
 // The refined solve is bound by the FP64 pipe, which leaves the other pipes and the memory
 // system to the location work of the other warps.
+// Resident blocks per SM of k_p2m_tab with the refined solve: 7 (72 registers; 5, 6, 7, 8
+// measured 1.123, 1.064, 1.048, 1.054 ms at 1025^2 nodes / 2048^2 particles).
+#ifndef PFEM_TAB_REF_MIN_BLOCKS
+#define PFEM_TAB_REF_MIN_BLOCKS 7
+#endif
+template <typename S, int REFINE> constexpr int tab_min_blocks()
+{
+    return sizeof(S) == 8 || REFINE == REFINE_NONE ? solve_min_blocks<S, REFINE>() : PFEM_TAB_REF_MIN_BLOCKS;
+}
+
 template <typename P, typename V, typename R, typename S, int REFINE>
-__global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_tab(P2MArgs a, StarTab t)
+__global__ void __launch_bounds__(128, tab_min_blocks<S, REFINE>()) k_p2m_tab(P2MArgs a, StarTab t)
 {
     const int I = blockIdx.x * 16 + (threadIdx.x & 15);
     const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
