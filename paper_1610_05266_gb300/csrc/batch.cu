@@ -264,6 +264,37 @@ __global__ void __launch_bounds__(256, PFEM_GEOM_MIN_BLOCKS / 2) k_p2m_batch_geo
     }
 }
 
+// The table path's fast pass of every problem in one persistent kernel (as k_p2m_tab: location
+// from the star table, edge solves and apply per node, no node records).
+template <typename P, typename V, typename R, typename S, int REFINE>
+__global__ void __launch_bounds__(256, tab_min_blocks<S, REFINE>() / 2) k_p2m_batch_tab(
+    const BPlanDev *pl, int shape_idx, P2MArgs base, unsigned long long *counter, StarTab tab)
+{
+    __shared__ long long item;
+    if (!totals_ok(pl, nullptr, &tab, base.status)) return;
+    const int TY = blockDim.x / 16;
+    const long long total = pl->n_items[shape_idx];
+    const long long *tp = plan_tiles(pl, shape_idx);
+    for (int guard = 0; guard < (1 << 30); ++guard) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = item;
+        if (it >= total) break;
+        const int p = find_item(tp, pl->P, it);
+        const BDesc d = plan_desc(pl)[p];
+        const long long t = it - tp[p];
+        const int tiles_x = (d.n + 15) / 16;
+        const int I = (int)(t % tiles_x) * 16 + (threadIdx.x & 15);
+        const int J = (int)(t / tiles_x) * TY + (threadIdx.x >> 4);
+        if (I >= d.n || J >= d.n) continue;
+        P2MArgs a;
+        problem_args(a, base, d);
+        problem_out<V>(a, base, d);
+        tab_node<P, V, R, S, REFINE>(a, tab, I, J);
+    }
+}
+
 // The fix pass over the batch's queued nodes (batch-wide indices), each with its problem's
 // bins, the widest search radius and FP64 SVD solves.
 template <typename P, typename V, typename R, int SHAPE>
@@ -434,10 +465,16 @@ static cudaError_t p2m_batch_t(const void *plan, const P2MArgs &base, int shape_
         k_star_list_batch<<<num_sms() * 8, BSTAR, 0, s>>>(pl, base, w.tab);
         k_star_retry_batch<true><<<num_sms() * PFEM_RETRY_BLOCKS, 64, 0, s>>>(pl, base, w.tab);
         k_star_retry_batch<false><<<num_sms() * 4, 64, 0, s>>>(pl, base, w.tab);
-        k_p2m_batch_geom<P, V, R><<<blocks, 16 * TYs[shape_idx], 0, s>>>(pl, shape_idx, base, counter,
-                                                                      w.tab, w.recs);
-        k_p2m_solve<P, V, R, S, REF><<<(unsigned)((w.recs.nodes + 127) / 128), 128, 0, s>>>(base, w.recs);
-        count_launch(5);
+        if (REF != REFINE_FF) {      // one kernel, as the single-problem table path
+            k_p2m_batch_tab<P, V, R, S, REF><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
+                pl, shape_idx, base, counter, w.tab);
+            count_launch(4);
+        } else {
+            k_p2m_batch_geom<P, V, R><<<blocks, 16 * TYs[shape_idx], 0, s>>>(pl, shape_idx, base,
+                                                                          counter, w.tab, w.recs);
+            k_p2m_solve<P, V, R, S, REF><<<(unsigned)((w.recs.nodes + 127) / 128), 128, 0, s>>>(base, w.recs);
+            count_launch(5);
+        }
     } else {
         k_p2m_batch<P, V, R, S, REF, SHAPE><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
             pl, shape_idx, base, counter);

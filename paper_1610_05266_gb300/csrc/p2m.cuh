@@ -836,12 +836,11 @@ template <typename S, int REFINE> constexpr int tab_min_blocks()
     return sizeof(S) == 8 || REFINE == REFINE_NONE ? solve_min_blocks<S, REFINE>() : PFEM_TAB_REF_MIN_BLOCKS;
 }
 
+// Node (I, J) of the problem of a (mesh output a.out; queue entries and error details at node
+// a.noff + J * a.n + I of the batch).
 template <typename P, typename V, typename R, typename S, int REFINE>
-__global__ void __launch_bounds__(128, tab_min_blocks<S, REFINE>()) k_p2m_tab(P2MArgs a, StarTab t)
+__device__ __forceinline__ void tab_node(const P2MArgs &a, const StarTab &t, int I, int J)
 {
-    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
-    if (I >= a.n || J >= a.n) return;
     const int nc = a.n - 1;
     const int Iu = I == nc ? 0 : I, Ju = J == nc ? 0 : J;
     const long long node = (long long)J * a.n + I;
@@ -886,12 +885,21 @@ __global__ void __launch_bounds__(128, tab_min_blocks<S, REFINE>()) k_p2m_tab(P2
         }
     }
     if (st != 0) {
-        st = defer_or_error(a, st, node);
-        if (st < 0) record_error(a.status, -st, node);
+        st = defer_or_error(a, st, a.noff + node);
+        if (st < 0) record_error(a.status, -st, a.noff + node);
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = (R)nan_of<R>();
     }
     store_vals<V, R>((V *)a.out, node, a.C, acc);
+}
+
+template <typename P, typename V, typename R, typename S, int REFINE>
+__global__ void __launch_bounds__(128, tab_min_blocks<S, REFINE>()) k_p2m_tab(P2MArgs a, StarTab t)
+{
+    const int I = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int J = blockIdx.y * 8 + (threadIdx.x >> 4);
+    if (I >= a.n || J >= a.n) return;
+    tab_node<P, V, R, S, REFINE>(a, t, I, J);
 }
 
 }  // namespace pfem
