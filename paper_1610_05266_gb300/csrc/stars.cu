@@ -8,7 +8,7 @@
 
 namespace pfem {
 
-__global__ void __launch_bounds__(STAR_TPB) k_star_list(Bins B, int R0, StarTab t, DevStatus *st)
+__global__ void __launch_bounds__(STAR_TPB, 6) k_star_list(Bins B, int R0, StarTab t, DevStatus *st)
 {
     __shared__ float2 sxy[STAR_KL * STAR_TPB];
     __shared__ unsigned skey[STAR_KL * STAR_TPB];

@@ -113,7 +113,8 @@ __device__ __forceinline__ unsigned pack_key(float x, float y, int k)
     return ((unsigned)(a * 33554432.0f) << 5) | (unsigned)k;
 }
 
-// Sort KLC packed keys (bitonic network, unrolled: the array stays in registers).
+// Sort KLC packed keys (bitonic network, unrolled: the array stays in registers; Batcher's
+// odd-even merge network, 63 instead of 80 compare-exchanges for 16 keys, measured slower).
 template <int KLC> __device__ __forceinline__ void sort_keys(unsigned (&w)[KLC])
 {
 #pragma unroll
@@ -230,7 +231,8 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     // Graham scan, cyclically from u0.  Is the image of c to the left of the images of a -> b,
     // i.e. c outside the circle through v, a, b?  FP32 filter on
     // det = la (b x c) - lb (a x c) + lc (a x b), whose terms are bounded by
-    // la lb + lc (la + lb) (|p x q| <= (lp + lq) / 2); the exact predicate when undecided.
+    // la lb + lc (la + lb) <= 3 D^4 (|p x q| <= (lp + lq) / 2, every l <= D^2): one bound for the
+    // whole star, 2^-19 of that; the exact predicate when undecided.
     // The two top entries of the stack are kept in registers.
     auto xyl = [&](int k, float &x, float &y, float &l) {
         const float2 t = L.xy[k * S];
@@ -244,10 +246,10 @@ __device__ __forceinline__ int star_hull(const Bins &B, int v, uint2 pv, const R
     float ab = 0.f;
     L.stk[0] = (unsigned char)u0;
     int sp = 1;
+    const float bnd = 5.7220458984375e-06f * D2 * D2;    // 3 x 2^-19 x D^4
     auto left = [&](int c, float cx, float cy, float lc) -> bool {
         const float bc = fmaf(bx, cy, -by * cx), ac = fmaf(ax, cy, -ay * cx);
         const float det = fmaf(la, bc, fmaf(-lbv, ac, lc * ab));
-        const float bnd = 1.9073486328125e-06f * fmaf(la, lbv, lc * (la + lbv));
         if (det > bnd) return true;
         if (det < -bnd) return false;
         const uint2 qa = __ldg(B.q + L.s[ia * S]), qb = __ldg(B.q + L.s[ib * S]),

@@ -90,6 +90,24 @@ def test_context_options_and_last_error(lib):
     lib.pfem_destroy(null)
 
 
+def test_values_and_stage_events_need_a_context(lib):
+    """pfem_set_values_event / pfem_set_stage_events belong to a context: without one they are
+    refused with a message; with one, setting and clearing them succeeds on the host (nothing
+    is launched until a P2M call)."""
+    null = ctypes.c_void_p(0)
+    assert lib.pfem_set_values_event(null, null) == 1
+    assert b"needs a context" in lib.pfem_last_error(None)
+    assert lib.pfem_set_stage_events(null, null, 0) == 1
+    h = ctypes.c_void_p()
+    assert lib.pfem_create(ctypes.byref(h), None) == 0
+    assert lib.pfem_set_values_event(h, ctypes.c_void_p(0x1234)) == 0   # stored, not used here
+    assert lib.pfem_set_values_event(h, null) == 0
+    assert lib.pfem_set_stage_events(h, null, 9) == 1
+    assert b"0..8" in lib.pfem_last_error(h)
+    assert lib.pfem_set_stage_events(h, null, 0) == 0
+    lib.pfem_destroy(h)
+
+
 def test_python_context_wrapper():
     import paper_1610_05266_gb300 as P
     ctx = P.Context(walk_max_steps=3, star_capacity=5)
