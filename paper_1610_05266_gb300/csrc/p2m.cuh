@@ -59,50 +59,168 @@ __device__ __forceinline__ int defer_or_error(const P2MArgs &a, int st, long lon
 }
 
 // Minimum-norm least-squares solution of P A = b (App. A: the SVD with rank detection), for the
-// 6 x k matrix P whose columns are the stencil's monomial vectors; pt holds P^T (k rows of 6)
-// and is overwritten.  One-sided (Hestenes) Jacobi (jacobi_svd): plane rotations of pairs of the
-// six columns of P^T until all are mutually orthogonal, accumulated in V, so that P^T V = W with
-// orthogonal columns w_j = sigma_j u_j (left in pt) and sig2[j] = sigma_j^2.  Then P = V W^T and
+// 6 x k matrix P whose columns are the stencil's monomial vectors; pt holds P^T (k rows of 6,
+// k <= SVD_ROWS) and is overwritten.  jacobi_svd gives P^T V = W with orthogonal columns
+// w_j = sigma_j u_j (left in pt), V orthogonal and sig2[j] = sigma_j^2; then P = V W^T and
 // A = sum_j (v_j . b / sigma_j^2) w_j over the singular values above max(k, 6) eps sigma_max
 // (smaller ones are rank deficiency).
+//
+// Steps: a Householder QR P^T = Q [R; 0] (Golub & Van Loan, 5.2), which keeps the singular
+// values; one-sided (Hestenes) Jacobi on the 6 x 6 factor R -- plane rotations of pairs of its
+// columns until all are mutually orthogonal, accumulated in V, so that R V = W6 -- with R, V and
+// the rotations in registers; then W = Q [W6; 0].  The sweeps, the long part, so run on 6 rows
+// instead of k.
+constexpr int SVD_ROWS = 32;
+
+// Householder QR of pt (k x 6): R (6 x 6; rows past min(k, 6) zero) and the reflections, v_j
+// kept in pt[j..k-1][j] with vv[j] = v_j . v_j (0: no reflection).
+static __device__ __forceinline__ void householder_qr(int k, double (*pt)[6], double R[6][6],
+                                                      double vv[6])
+{
+    const int m = k < 6 ? k : 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) R[i][j] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        vv[j] = 0.0;
+        if (j >= m) continue;
+        double nx = 0.0;
+        for (int i = j; i < k; ++i) nx = fma(pt[i][j], pt[i][j], nx);
+        const double x0 = pt[j][j];
+        const double alpha = x0 >= 0.0 ? -sqrt(nx) : sqrt(nx);
+        if (nx > 0.0) {
+            pt[j][j] = x0 - alpha;
+            vv[j] = 2.0 * (nx + fabs(x0) * sqrt(nx));     // v.v = 2 (|x|^2 - alpha x0)
+#pragma unroll
+            for (int c = j + 1; c < 6; ++c) {
+                double d = 0.0;
+                for (int i = j; i < k; ++i) d = fma(pt[i][j], pt[i][c], d);
+                const double f = 2.0 * d / vv[j];
+                for (int i = j; i < k; ++i) pt[i][c] = fma(-f, pt[i][j], pt[i][c]);
+            }
+        }
+        R[j][j] = nx > 0.0 ? alpha : x0;
+#pragma unroll
+        for (int c = j + 1; c < 6; ++c) R[j][c] = pt[j][c];
+    }
+}
+
+// out[0..k) = Q [y; 0] = H_0 H_1 ... H_5 [y; 0] with the reflections of householder_qr.
+static __device__ __forceinline__ void apply_q(int k, const double (*pt)[6], const double vv[6],
+                                               const double y[6], double *out)
+{
+    for (int i = 0; i < k; ++i) out[i] = i < 6 ? y[i] : 0.0;
+#pragma unroll
+    for (int j = 5; j >= 0; --j) {
+        if (vv[j] == 0.0) continue;
+        double d = 0.0;
+        for (int i = j; i < k; ++i) d = fma(pt[i][j], out[i], d);
+        const double f = 2.0 * d / vv[j];
+        for (int i = j; i < k; ++i) out[i] = fma(-f, pt[i][j], out[i]);
+    }
+}
+
+// One-sided (Hestenes) Jacobi on R (6 x 6): plane rotations of pairs of its columns until all
+// are mutually orthogonal, accumulated in V, so that R V = W6 (left in R), sig2[j] = |w6_j|^2.
+//  - Each sweep takes the 15 column pairs in the round-robin order of 5 rounds of 3 disjoint
+//    pairs, so that three rotations are independent.
+//  - A rotation's tangent comes from FP32 arithmetic: any exact rotation keeps the singular
+//    values, and its angle only sets how fast the off-diagonal products fall.  c = 1/sqrt(1+t^2)
+//    and s = c t are formed in FP64 from that t, so the rotation is orthogonal to FP64
+//    precision.  (FP64 divides and square roots are long instruction sequences on the narrow
+//    FP64 pipe.)
+//  - Columns whose squared norm is below 1e-31 of ||R||_F^2 are left alone: the rank detection
+//    drops them (its threshold is above (6 eps)^2 sigma_max^2 >= 1.7e-30 ||R||_F^2 / 6), and their
+//    rounding noise would otherwise keep a sweep from converging.
+static __device__ __forceinline__ void jacobi6(double R[6][6], double V[6][6], double sig2[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    double f2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) f2 = fma(R[i][j], R[i][j], f2);
+    const double tiny2 = 1e-31 * f2;
+    constexpr int RR[5][3][2] = {{{0, 1}, {2, 3}, {4, 5}}, {{0, 2}, {1, 4}, {3, 5}},
+                                 {{0, 3}, {1, 5}, {2, 4}}, {{0, 4}, {1, 3}, {2, 5}},
+                                 {{0, 5}, {1, 2}, {3, 4}}};
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        bool rotated = false;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const int p = RR[r][h][0], q = RR[r][h][1];
+                double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    al = fma(R[i][p], R[i][p], al);
+                    be = fma(R[i][q], R[i][q], be);
+                    ga = fma(R[i][p], R[i][q], ga);
+                }
+                if (!(ga * ga > 1e-30 * al * be) || al < tiny2 || be < tiny2) continue;
+                // tangent of the rotation angle in FP32: zeta = (be - al) / (2 ga)
+                const float gf = f32_trunc(ga), df = f32_trunc(be - al);
+                if (gf == 0.f) continue;        // |ga| below FP32's range: nothing to rotate
+                const float zf = df / (2.f * gf);
+                const float tf = copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f)));
+                if (!(tf != 0.f)) continue;     // |zeta| beyond 1e19: the angle is below FP64's
+                rotated = true;
+                const double t = f64_of(tf);
+                const double c = rsqrt(fma(t, t, 1.0)), s = c * t;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const double x = R[i][p], y = R[i][q];
+                    R[i][p] = fma(c, x, -s * y);
+                    R[i][q] = fma(s, x, c * y);
+                    const double u = V[i][p], w = V[i][q];
+                    V[i][p] = fma(c, u, -s * w);
+                    V[i][q] = fma(s, u, c * w);
+                }
+            }
+        }
+        if (!rotated) break;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double s2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s2 = fma(R[i][j], R[i][j], s2);
+        sig2[j] = s2;
+    }
+}
+
+// The SVD P^T V = W of the k x 6 matrix in pt (overwritten with W): householder_qr, jacobi6 on
+// R, then W = Q [W6; 0].
 static __device__ __forceinline__ void jacobi_svd(int k, double (*pt)[6], double V[6][6],
                                                   double sig2[6])
 {
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j < 6; ++j) V[i][j] = i == j ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        bool rotated = false;
-        for (int p = 0; p < 5; ++p)
-            for (int q = p + 1; q < 6; ++q) {
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    al = fma(pt[i][p], pt[i][p], al);
-                    be = fma(pt[i][q], pt[i][q], be);
-                    ga = fma(pt[i][p], pt[i][q], ga);
-                }
-                if (!(fabs(ga) > 1e-15 * sqrt(al * be))) continue;
-                rotated = true;
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                for (int i = 0; i < k; ++i) {
-                    const double x = pt[i][p], y = pt[i][q];
-                    pt[i][p] = c * x - s * y;
-                    pt[i][q] = s * x + c * y;
-                }
-                for (int i = 0; i < 6; ++i) {
-                    const double x = V[i][p], y = V[i][q];
-                    V[i][p] = c * x - s * y;
-                    V[i][q] = s * x + c * y;
-                }
-            }
-        if (!rotated) break;
+    double R[6][6], vv[6];
+    householder_qr(k, pt, R, vv);
+    jacobi6(R, V, sig2);
+    double W[SVD_ROWS][6];
+    for (int i = 0; i < k; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) W[i][c] = i < 6 ? R[i][c] : 0.0;
+#pragma unroll
+    for (int j = 5; j >= 0; --j) {
+        if (vv[j] == 0.0) continue;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double d = 0.0;
+            for (int i = j; i < k; ++i) d = fma(pt[i][j], W[i][c], d);
+            const double f = 2.0 * d / vv[j];
+            for (int i = j; i < k; ++i) W[i][c] = fma(-f, pt[i][j], W[i][c]);
+        }
     }
-    for (int j = 0; j < 6; ++j) {
-        double s2 = 0.0;
-        for (int i = 0; i < k; ++i) s2 = fma(pt[i][j], pt[i][j], s2);
-        sig2[j] = s2;
-    }
+    for (int i = 0; i < k; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pt[i][c] = W[i][c];
 }
 
 // Squared singular values kept by the rank detection: above (max(k, 6) eps)^2 sigma_max^2.
@@ -117,20 +235,23 @@ __device__ __forceinline__ double svd_threshold2(int k, const double sig2[6])
 static __device__ __noinline__ void minnorm_lsq(int k, double (*pt)[6], const double b[6],
                                                 double *A)
 {
-    double V[6][6], sig2[6], vb[6];
-    jacobi_svd(k, pt, V, sig2);
-    for (int j = 0; j < 6; ++j) {
-        double d = 0.0;
-        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
-        vb[j] = d;
-    }
+    // A = sum_j (v_j . b / sigma_j^2) w_j = Q [sum_j (v_j . b / sigma_j^2) w6_j; 0]
+    double R[6][6], vv[6], V[6][6], sig2[6];
+    householder_qr(k, pt, R, vv);
+    jacobi6(R, V, sig2);
     const double thr2 = svd_threshold2(k, sig2);
-    for (int i = 0; i < k; ++i) {
-        double a = 0.0;
-        for (int j = 0; j < 6; ++j)
-            if (sig2[j] > thr2) a = fma(vb[j] / sig2[j], pt[i][j], a);
-        A[i] = a;
+    double z[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        if (!(sig2[j] > thr2)) continue;
+        double d = 0.0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) d = fma(V[r][j], b[r], d);
+        const double cj = d / sig2[j];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) z[i] = fma(cj, R[i][j], z[i]);
     }
+    apply_q(k, pt, vv, z, A);
 }
 
 // Node position and minimal-image offsets in the compute precision R.
@@ -235,6 +356,7 @@ struct ArrStar {
 // SVD pass) or, in the SVD pass, -PFEM_ERR_CAPACITY (more than UMAX_SVD distinct particles).
 constexpr int UMAX = PFEM_UMAX; // fast pass: jittered lattices have at most about 20
 constexpr int UMAX_SVD = 32;   // SVD pass (the stencil masks are 32-bit)
+static_assert(UMAX_SVD <= SVD_ROWS, "stencils of the SVD pass fit jacobi_svd's rows");
 
 // SVD = true (the FP64 pass over queued nodes): each edge's coefficients are the minimum-norm
 // least-squares solution by SVD instead of the Cholesky solve of the moment system.
