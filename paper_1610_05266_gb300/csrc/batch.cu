@@ -464,7 +464,7 @@ static cudaError_t p2m_batch_t(const void *plan, const P2MArgs &base, int shape_
     if (SHAPE == PFEM_SHAPE_QUADRATIC && w.table) {
         k_star_list_batch<<<num_sms() * 8, BSTAR, 0, s>>>(pl, base, w.tab);
         k_star_retry_batch<true><<<num_sms() * PFEM_RETRY_BLOCKS, 64, 0, s>>>(pl, base, w.tab);
-        k_star_retry_batch<false><<<num_sms() * 4, 64, 0, s>>>(pl, base, w.tab);
+        k_star_retry_batch<false><<<num_sms() * PFEM_RETRY_REGION_BLOCKS, 64, 0, s>>>(pl, base, w.tab);
         if (REF != REFINE_FF) {      // one kernel, as the single-problem table path
             k_p2m_batch_tab<P, V, R, S, REF><<<blocks, 16 * TYs[shape_idx], 0, s>>>(
                 pl, shape_idx, base, counter, w.tab);

@@ -90,7 +90,7 @@ cudaError_t launch_star_table(const Bins &B, int R0, int rmax_far, const StarTab
     Bins Bf = B;
     Bf.rmax = std::max(B.rmax, rmax_far);
     k_star_retry_hull<<<num_sms() * PFEM_RETRY_BLOCKS, RETRY_TPB, 0, s>>>(Bf, R0, t, st);
-    k_star_retry<<<num_sms() * 4, 64, 0, s>>>(Bf, R0, t, st);
+    k_star_retry<<<num_sms() * PFEM_RETRY_REGION_BLOCKS, 64, 0, s>>>(Bf, R0, t, st);
     count_launch(3);
     return cudaGetLastError();
 }
