@@ -40,7 +40,8 @@ FLOP_PER_NODE_Q = 30 + 3 * (244 + 77 * STENCIL_MEAN) + 24
 FP64_FLOP_PER_NODE_RES = 3 * 21 * STENCIL_MEAN
 FP64_INST_PER_NODE_RES = 3 * 13 * STENCIL_MEAN
 FP32_LANES_PER_SM = 128
-FP64_PEAK_NOMINAL = 1.25      # TFLOP/s per GB300 (nominal, profiling recipe table); no measured value
+FP64_FMA_PER_SM_CLK = 2       # FP64 FMA per SM per clock: ncu's peak_sustained of
+                              # sm__sass_thread_inst_executed_op_dfma_pred_on on GB300
 
 
 def kernel_traffic(stage: str, solve: str):
@@ -342,6 +343,7 @@ def run_ours(args, world, rank, local):
     t_m2p = float(np.mean(m2p_ms)) * 1e-3
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * 2070.0e6 / 1e12   # TFLOP/s at the maximum SM clock
+    fp64_peak = sms * FP64_FMA_PER_SM_CLK * 2 * 2070.0e6 / 1e12
     p2m_flops = FLOP_PER_NODE_Q * nn
     # algorithmic bytes of the round trip: P2M reads pos + C vals per particle and writes C
     # per node; M2P reads pos per particle, C per node, writes C per particle (FP32)
@@ -357,14 +359,16 @@ def run_ours(args, world, rank, local):
                     "kernel": "k_p2m_tab (node location from the star table, FP32 Cholesky + "
                               "FP64-residual refinement, apply: one kernel)",
                     "achieved": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12,
-                    "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s (FP64)",
-                    "frac": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12 / FP64_PEAK_NOMINAL,
+                    "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                    "frac": FP64_FLOP_PER_NODE_RES * nn / t_dom / 1e12 / fp64_peak,
                     "algorithmic_flop_per_node": FP64_FLOP_PER_NODE_RES,
-                    "peak_source": "FP64 1.25 TFLOP/s per GB300 (nominal, of nominal: no measured FP64 peak)",
+                    "peak_source": f"derived: {sms} SMs (device query) x {FP64_FMA_PER_SM_CLK} FP64 FMA "
+                                   "per SM per clock (ncu peak counter) x 2 flop x 2070 MHz; nominal "
+                                   "1.25 TFLOP/s; no measured FP64 figure",
                     # the same residual counted in FP64 pipe instructions (FMA, MUL and ADD
                     # alike) against 2 per SM per clock (1.25 TFLOP/s / 2 / SMs / 2070 MHz)
                     "fp64_inst_per_node": FP64_INST_PER_NODE_RES,
-                    "fp64_pipe_frac": FP64_INST_PER_NODE_RES * nn / t_dom / (2 * sms * 2070.0e6)}
+                    "fp64_pipe_frac": FP64_INST_PER_NODE_RES * nn / t_dom / (FP64_FMA_PER_SM_CLK * sms * 2070.0e6)}
     else:
         roofline = {"bound": "alu", "kernel": {"star_table": "k_star_list + k_star_retry",
                                                 "geometry": "k_p2m_geom", "solve": "k_p2m_solve",
