@@ -128,14 +128,15 @@ const char *pfem_last_error(const pfem_ctx *ctx);
  * (count <= 8; 0 clears them).  Every later pfem_project_p2m with this context records them on
  * its stream at the boundaries of its stages when the star-table path runs: 0 before the fast
  * pass, 1 after the star table, 2 after the per-node geometry kernel, 3 after the solve kernel,
- * 4 after the fix pass (the other paths record 0 and 4 only).  The caller reads the intervals
+ * 4 after the fix pass (where one kernel locates the nodes and solves, 2 is recorded right
+ * before it and 3 after it; the other paths record 0 and 4 only).  The caller reads the intervals
  * with cudaEventElapsedTime after synchronising.  Recording adds no work to the kernels. */
 pfem_status pfem_set_stage_events(pfem_ctx *ctx, void *const *events, int32_t count);
 
 /* An event (cudaEvent_t as void*) that pfem_project_p2m calls made with this context wait on
  * (cudaStreamWaitEvent on the call's stream) right before their first kernel that reads the
- * particle values -- after the star table and the node records of the quadratic path, at the
- * start of the others; NULL (the default) clears it.  A caller can so copy the values on another
+ * particle values -- after the star table (and the node records, where they are written) of the
+ * quadratic path, at the start of the others; NULL (the default) clears it.  A caller can so copy the values on another
  * stream while the call works on the positions.  The event must have been recorded (or never
  * recorded: then the wait is a no-op) when the call is made. */
 pfem_status pfem_set_values_event(pfem_ctx *ctx, void *event);
@@ -246,10 +247,11 @@ pfem_status pfem_shape_quadratic(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N
  * from byte 512 (8 bytes per node; with ws_bytes < 520 there is no queue and such nodes record
  * PFEM_ERR_DEGENERATE or PFEM_ERR_CAPACITY), then, for the quadratic apply form, 136 bytes of
  * record per node and the star table (72 bytes per particle).  With room for them the fast
- * pass is the star table of every particle (see pfem_delaunay_stars), a per-node geometry
- * kernel that locates the node and builds its particle set from the table, and a solve kernel
- * for the three edge systems and the weights; with less, one kernel searches every node's
- * stars itself (same results, slower).  The workspace of pfem_workspace_size() has room for
+ * pass is the star table of every particle (see pfem_delaunay_stars) and one kernel that, per
+ * node, locates it with the table, builds its particle set and solves the three edge systems;
+ * the float-float solve (PFEM_SOLVE_F32_REFINED_FF) splits that kernel in two, a geometry
+ * kernel writing the node records and a solve kernel reading them.  With less room, one kernel
+ * searches every node's stars itself (same results, slower).  The workspace of pfem_workspace_size() has room for
  * everything. */
 pfem_status pfem_project_p2m(pfem_ctx *ctx, int32_t n, int32_t nb, int64_t N, const void *pos_sorted,
                              pfem_dtype pos_t, const uint32_t *q_sorted,

@@ -89,11 +89,13 @@ static bool set_table(NodeRecs &r, StarTab &t, void *ws, size_t ws_bytes, long l
 }
 
 // P2M: the fast pass over all nodes, then the fix pass over the nodes it queued.  With quadratic
-// shape functions, the apply form and room for the table, the fast pass is the star table, the
+// shape functions, the apply form and room for the table, the fast pass is the star table and
+// then k_p2m_tab (location, edge solves and apply per node), or, for the float-float solve, the
 // geometry kernel (node records) and the solve kernel; otherwise one kernel that searches the
 // stars per node.
 // Stage events (when the caller's context has them): 0 before the fast pass, 1 after the star
-// table, 2 after the geometry kernel, 3 after the solve kernel, 4 after the fix pass.
+// table, 2 after the geometry kernel (right before k_p2m_tab), 3 after the solve kernel (after
+// k_p2m_tab), 4 after the fix pass.
 template <typename P, typename V, typename R, typename S, int REF, int SHAPE, bool W>
 static cudaError_t go(const GeoArgs &g, const P2MArgs &a, cudaStream_t s,
                       const NodeRecs *rec = nullptr, const StarTab *tab = nullptr)

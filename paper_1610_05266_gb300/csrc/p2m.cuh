@@ -705,12 +705,12 @@ __global__ void __launch_bounds__(128) k_p2m_fix(P2MArgs a)
     }
 }
 
-// ---------------------------------------------------------------- two-kernel fused P2M
-// The quadratic apply path with FP32 solves as two kernels, so that the star search (large
-// thread-private state, latency bound) and the moment solves (register-heavy arithmetic) each
-// get their own register budget: k_p2m_geom locates the node and builds its particle set, k_p2m_solve
-// solves the three edge systems and applies the weights.  They hand over a per-node record,
-// one array per field so that both kernels access it coalesced.
+// ---------------------------------------------------------------- two-kernel P2M
+// The table path as two kernels, each with its own register budget: k_p2m_geom locates the node
+// and builds its particle set from the star table (memory latency bound), k_p2m_solve solves the
+// three edge systems and applies the weights.  They hand over a per-node record, one array per
+// field so that both kernels access it coalesced.  The float-float solve and the adjoint take
+// this form; the other forward solves run both halves in k_p2m_tab.
 struct NodeRecs {
     int *meta;          // [nodes] nu | vi0 << 5 | vi1 << 10 | vi2 << 15, or -1: no record
     unsigned *mask;     // [3][nodes] vm[e]
