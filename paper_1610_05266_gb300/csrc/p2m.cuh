@@ -433,7 +433,14 @@ __device__ __forceinline__ int node_u_solve(const P2MArgs &a, const NodePos<P, R
         x = S(dx);
         y = S(dy);
     };
-#pragma unroll
+    // The three edges in a loop that is not unrolled: one copy of the edge code keeps the
+    // kernels' instruction footprint and register spills down (fused kernel with the refined
+    // solve: 1.047 -> 1.010 ms at 1025^2 nodes / 2048^2 particles; spills 164 -> 40 bytes).
+#ifndef PFEM_EDGE_UNROLL
+#define PFEM_EDGE_UNROLL 1
+#endif
+    constexpr int edge_unroll = PFEM_EDGE_UNROLL;
+#pragma unroll edge_unroll
     for (int e = 0; e < 3; ++e) {
         const int f = e == 2 ? 0 : e + 1;
         const unsigned mask = vm[e] | vm[f];
@@ -948,10 +955,10 @@ __global__ void __launch_bounds__(128, solve_min_blocks<S, REFINE>()) k_p2m_solv
 // builds its particle set and solves its three edge systems, without a node record in between.
 // The refined solve is bound by the FP64 pipe, which leaves the other pipes and the memory
 // system to the location work of the other warps.
-// Resident blocks per SM of k_p2m_tab with the refined solve: 7 (72 registers; 5, 6, 7, 8
-// measured 1.123, 1.064, 1.048, 1.054 ms at 1025^2 nodes / 2048^2 particles).
+// Resident blocks per SM of k_p2m_tab with the refined solve: 8 (64 registers; with the edge
+// loop rolled 6, 7, 8 measured 1.051, 1.011, 1.000 ms at 1025^2 nodes / 2048^2 particles).
 #ifndef PFEM_TAB_REF_MIN_BLOCKS
-#define PFEM_TAB_REF_MIN_BLOCKS 7
+#define PFEM_TAB_REF_MIN_BLOCKS 8
 #endif
 template <typename S, int REFINE> constexpr int tab_min_blocks()
 {
