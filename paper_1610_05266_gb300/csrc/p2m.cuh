@@ -164,14 +164,26 @@ static __device__ __forceinline__ void jacobi6(double R[6][6], double V[6][6], d
                     ga = fma(R[i][p], R[i][q], ga);
                 }
                 if (!(ga * ga > 1e-30 * al * be) || al < tiny2 || be < tiny2) continue;
-                // tangent of the rotation angle in FP32: zeta = (be - al) / (2 ga)
-                const float gf = f32_trunc(ga), df = f32_trunc(be - al);
-                if (gf == 0.f) continue;        // |ga| below FP32's range: nothing to rotate
-                const float zf = df / (2.f * gf);
-                const float tf = copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f)));
-                if (!(tf != 0.f)) continue;     // |zeta| beyond 1e19: the angle is below FP64's
+                // tangent of the rotation angle: zeta = (be - al) / (2 ga), in FP32 while the
+                // operands are well inside its range (near-coincident particles can make the
+                // scaled monomials huge), else in FP64
+                double t;
+                const double dba = be - al;
+                // binary exponents from the bit patterns (integer pipes): |dba| < 2^96 and
+                // 2^-95 <= |ga| < 2^96
+                const int ed = (__double2hiint(dba) >> 20) & 0x7ff, eg = (__double2hiint(ga) >> 20) & 0x7ff;
+                if (ed < 1023 + 96 && eg > 1023 - 96 && eg < 1023 + 96) {
+                    const float gf = f32_trunc(ga), df = f32_trunc(dba);
+                    const float zf = df / (2.f * gf);
+                    const float tf = copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f)));
+                    if (!(tf != 0.f)) continue; // |zeta| beyond 1e19: the angle is below FP64's
+                    t = f64_of(tf);
+                } else {
+                    const double zeta = dba / (2.0 * ga);
+                    t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                    if (!(t != 0.0)) continue;
+                }
                 rotated = true;
-                const double t = f64_of(tf);
                 const double c = rsqrt(fma(t, t, 1.0)), s = c * t;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
