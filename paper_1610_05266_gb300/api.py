@@ -445,8 +445,10 @@ class HostRoundTrip:
     buffer sets while the previous step computes; P2M waits for the values only before its first
     kernel that reads them (the context's values event, pfem_set_values_event); the result goes
     back on a third stream while the next step runs.  step() returns at once; wait() blocks until
-    the last step's result is in its host buffer.  proj must have a context (one is created if
-    it has none)."""
+    the last step's result is in its host buffer.  The copies are asynchronous: a step's host
+    input buffers must not be rewritten before inputs_copied() (or wait()) has returned, and
+    its output buffer must not be read before wait().  proj must have a context (one is created
+    if it has none)."""
 
     def __init__(self, proj: "Projector", C: int, dtype=torch.float32, shape=PFEM_SHAPE_QUADRATIC,
                  solve=None, m2p_shape=PFEM_SHAPE_LINEAR, stream=None):
@@ -498,6 +500,11 @@ class HostRoundTrip:
 
     def wait(self):
         self.ev_out.synchronize()
+
+    def inputs_copied(self):
+        """Block until the last step's input copies have run (its host inputs may be reused)."""
+        if self.k > 0:
+            self.ev_vals[(self.k - 1) & 1].synchronize()
 
     def join(self, stream=None):
         """Make `stream` (default: the compute stream) wait for the last result's copy."""

@@ -155,6 +155,7 @@ def test_host_round_trip_matches_device_steps(P):
     outs = [torch.empty((M * M, C), dtype=torch.float32).pin_memory() for _ in range(6)]
     for k, out_h in enumerate(outs):
         rt.step(*sets[k % 2], out_h)
+    rt.inputs_copied()
     rt.wait()
     proj.check()
     for k, out_h in enumerate(outs):
