@@ -894,16 +894,16 @@ __global__ void __launch_bounds__(128) k_p2m_fix_tab(P2MArgs a, StarTab t)
     }
 }
 
-// Resident 128-thread blocks per SM of the solve kernel: 8 (64 registers) hold the FP32 moment
-// system without spills (sweep 8, 10, 12: 8).  The refined solves take 6 (80 registers, a few
-// bytes of spills): the FP64 residual keeps the narrow FP64 pipe busy only with many warps in
-// flight (4, 6, 8: 6; one to three persistent blocks per SM measured 1.1 to 2.4 times slower).
-// (FP64 solves keep the single fused kernel, whose larger occupancy measured faster.)
+// Resident 128-thread blocks per SM of the solve kernel (the two-kernel form: the float-float
+// refinement): 8 (64 registers) for the FP32 moment system (sweep 8, 10, 12: 8), and 8 as well
+// for the refined solves with the edge loop rolled (float-float: 6 -> 8 blocks 0.553 -> 0.536
+// ms at 1025^2 nodes / 2048^2 particles).  A refined solve needs many warps in flight to keep
+// the FP64 pipe busy: one to three persistent blocks per SM measured 1.1 to 2.4 times slower.
 #ifndef PFEM_SOLVE_MIN_BLOCKS
 #define PFEM_SOLVE_MIN_BLOCKS 8
 #endif
 #ifndef PFEM_SOLVE_REF_MIN_BLOCKS
-#define PFEM_SOLVE_REF_MIN_BLOCKS 6
+#define PFEM_SOLVE_REF_MIN_BLOCKS 8
 #endif
 template <typename S, int REFINE> constexpr int solve_min_blocks()
 {
