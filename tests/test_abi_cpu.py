@@ -90,6 +90,19 @@ def test_context_options_and_last_error(lib):
     lib.pfem_destroy(null)
 
 
+def test_options_struct_matches_the_header(lib):
+    """pfem_options as the binding lays it out is the header's struct: 16 int32 fields
+    (64 bytes), and pfem_options_default writes inside it (a canary after it stays intact)."""
+    import paper_1610_05266_gb300._lib as L
+    assert ctypes.sizeof(L.Options) == 64
+    buf = (ctypes.c_uint8 * (ctypes.sizeof(L.Options) + 64))(*([0xA5] * (ctypes.sizeof(L.Options) + 64)))
+    lib.pfem_options_default(ctypes.cast(buf, ctypes.c_void_p))
+    assert all(b == 0xA5 for b in bytes(buf)[ctypes.sizeof(L.Options):])
+    got = L.Options.from_buffer_copy(bytes(buf)[:ctypes.sizeof(L.Options)])
+    assert (got.walk_max_steps, got.star_capacity, got.node_capacity) == (64, 16, 24)
+    assert all(r == 0 for r in got.reserved)
+
+
 def test_values_and_stage_events_need_a_context(lib):
     """pfem_set_values_event / pfem_set_stage_events belong to a context: without one they are
     refused with a message; with one, setting and clearing them succeeds on the host (nothing
